@@ -1,0 +1,244 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things other than itself: the paper's printed ordering and
+matrices (tests/golden), hand-derived closed forms, exact integer arithmetic, an explicit
+Kronecker-product formulation of the trace, library routines (scipy's Sylvester Hadamard
+matrix), invariants of the Pauli basis, and a restatement of the paper's Gray-code variant.
+"""
+import ast
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from oracle import kron
+from paper_2401_16378_gb300 import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand(N, seed):
+    return workloads.gaussian_complex(N, seed)
+
+
+def test_threads_positive():
+    assert oracle.default_threads() >= 1
+
+
+def test_pauli_matrices_fixture():
+    """Eq. (3): the four Pauli matrices used by both oracle formulations."""
+    rows = {}
+    with open(os.path.join(GOLDEN, "pauli_matrices.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, *vals = line.split()
+            rows[name] = np.array([complex(ast.literal_eval(v)) for v in vals]).reshape(2, 2)
+    for name, P in zip("IXYZ", kron.PAULIS):
+        np.testing.assert_array_equal(P, rows[name])
+        # the C oracle decomposes each Pauli matrix into a one-hot vector
+        c = oracle.decompose_full(rows[name])
+        np.testing.assert_array_equal(c, np.eye(4)["IXYZ".index(name)])
+
+
+def test_eq2_ordering_fixture():
+    """Eq. (2): c_1 multiplies 1(x)X, c_4 multiplies X(x)1, c_15 multiplies Z(x)Z, ..."""
+    with open(os.path.join(GOLDEN, "eq2_ordering_n2.txt")) as f:
+        pairs = [line.split() for line in f if line.strip() and not line.startswith("#")]
+    assert len(pairs) == 6
+    P = dict(zip("IXYZ", kron.PAULIS))
+    for n_str, lab in pairs:
+        n = int(n_str)
+        assert kron.label(n, 2) == lab
+        explicit = np.kron(P[lab[0]], P[lab[1]])  # leftmost factor first
+        np.testing.assert_array_equal(kron.pauli_tensor(n, 2), explicit)
+        c = oracle.decompose_full(explicit)
+        expect = np.zeros(16)
+        expect[n] = 1
+        np.testing.assert_array_equal(c, expect)
+
+
+def test_one_qubit_closed_form():
+    """Eq. (4) at N=1 by hand: c_I=(g00+g11)/2, c_X=(g01+g10)/2, c_Y=i(g01-g10)/2, c_Z=(g00-g11)/2.
+
+    For G = [[1, 2], [3, 4]]: Tr(Y G) = (-i)(3) + (i)(2) = -i, so c_Y = -0.5i, and
+    c = (2.5, 2.5, -0.5i, -1.5).
+    """
+    G = np.array([[1, 2], [3, 4]], dtype=np.complex128)
+    c = oracle.decompose_full(G)
+    np.testing.assert_array_equal(c, np.array([2.5, 2.5, -0.5j, -1.5]))
+    g = _rand(1, 7)
+    c = oracle.decompose_full(g)
+    expect = np.array([(g[0, 0] + g[1, 1]) / 2, (g[0, 1] + g[1, 0]) / 2, 1j * (g[0, 1] - g[1, 0]) / 2,
+                       (g[0, 0] - g[1, 1]) / 2])
+    np.testing.assert_allclose(c, expect, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_matches_kronecker_trace(N):
+    """Eq. (13) (the C oracle) against Tr(P_n G)/2^N with explicit Kronecker tensors (Eq. (4))."""
+    G = _rand(N, 100 + N)
+    np.testing.assert_allclose(oracle.decompose_full(G), kron.decompose(G), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_integer_input_is_exact(N):
+    """Integer entries: every partial sum is exact in FP64, so both formulations agree bitwise."""
+    G = workloads.integer_complex(N, 5 + N)
+    np.testing.assert_array_equal(oracle.decompose_full(G), kron.decompose(G))
+
+
+def test_one_hot_for_every_pauli_string():
+    N = 3
+    for n in range(4 ** N):
+        c = oracle.decompose_full(kron.pauli_tensor(n, N))
+        assert c[n] == 1 and np.count_nonzero(c) == 1
+
+
+def test_identity():
+    c = oracle.decompose_full(np.eye(32, dtype=np.complex128))
+    assert c[0] == 1 and np.count_nonzero(c) == 1
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_reconstruction(N):
+    """Eq. (1): G = sum_n c_n P_n, with both compose formulations."""
+    G = _rand(N, 200 + N)
+    c = oracle.decompose_full(G)
+    np.testing.assert_allclose(oracle.compose_full(c), G, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(kron.compose(c), G, rtol=0, atol=1e-13)
+
+
+def test_compose_one_hot_is_pauli_tensor():
+    N = 2
+    for n in range(16):
+        e = np.zeros(16, dtype=np.complex128)
+        e[n] = 1
+        np.testing.assert_array_equal(oracle.compose_full(e), kron.pauli_tensor(n, N))
+
+
+def test_parseval():
+    """The P_n are orthogonal with Tr(P_n^H P_m) = 2^N delta: sum |c|^2 = 2^-N ||G||_F^2."""
+    N = 5
+    G = _rand(N, 300)
+    c = oracle.decompose_full(G)
+    assert np.isclose(np.sum(np.abs(c) ** 2), np.linalg.norm(G) ** 2 / 2 ** N, rtol=1e-13)
+
+
+def test_hermitian_gives_real_coefficients():
+    N = 5
+    G = workloads.hermitian_complex(N, 301)
+    c = oracle.decompose_full(G)
+    assert np.max(np.abs(c.imag)) <= 1e-15 * np.max(np.abs(G))
+
+
+def test_diagonal_input_is_sylvester_hadamard():
+    """Diagonal G: only tensors of I and Z survive, and they form 2^-N H diag(G) (scipy's H)."""
+    N = 5
+    D = 1 << N
+    d = _rand(N, 302)[0]
+    c = oracle.decompose_full(np.diag(d))
+    H = scipy.linalg.hadamard(D)
+    expect = (H @ d) / D
+    # the tensor whose operator t is Z when bit t of z is set, I otherwise
+    n_of_z = [sum(3 << (2 * t) for t in range(N) if (z >> t) & 1) for z in range(D)]
+    np.testing.assert_allclose(c[n_of_z], expect, rtol=0, atol=1e-14)
+    mask = np.ones(4 ** N, dtype=bool)
+    mask[n_of_z] = False
+    assert np.count_nonzero(c[mask]) == 0
+
+
+def test_kronecker_factorisation():
+    """decompose(A (x) B)[nA 4^NB + nB] = a[nA] b[nB] (the Pauli basis is a tensor basis)."""
+    A, B = _rand(2, 303), _rand(2, 304)
+    a, b = oracle.decompose_full(A), oracle.decompose_full(B)
+    c = oracle.decompose_full(np.kron(A, B))
+    np.testing.assert_allclose(c, np.outer(a, b).ravel(), rtol=0, atol=1e-14)
+
+
+def test_linearity():
+    A, B = _rand(4, 305), _rand(4, 306)
+    s = 0.25 - 1.5j
+    np.testing.assert_allclose(oracle.decompose_full(A + s * B),
+                               oracle.decompose_full(A) + s * oracle.decompose_full(B), rtol=0, atol=1e-14)
+
+
+def test_sampled_equals_full():
+    N = 5
+    G = _rand(N, 307)
+    full = oracle.decompose_full(G)
+    idx = workloads.sample_indices(N, 308, k=200)
+    np.testing.assert_array_equal(oracle.decompose_at(G, idx), full[idx.astype(np.int64)])
+
+
+def _gray_code_coefficient(G, n, N):
+    """The paper's fast variant restated (Sec. 3 and Eq. (14)): visit i in Gray-code order and
+    update lambda by one factor per step instead of rebuilding it."""
+    P = kron.PAULIS
+    dig = kron.digits(n, N)
+    m = sum(1 << t for t in range(N) if dig[t] in (1, 2))
+
+    def beta(t, i):
+        a = (i >> t) & 1
+        return P[dig[t]][a, a ^ ((m >> t) & 1)]
+
+    lam = np.prod([beta(t, 0) for t in range(N)]) if N else 1.0
+    total = lam * G[m, 0]
+    prev = 0
+    for k in range(1, 1 << N):
+        i = k ^ (k >> 1)
+        t = (i ^ prev).bit_length() - 1
+        lam = lam * beta(t, i) / beta(t, prev)
+        total += lam * G[i ^ m, i]
+        prev = i
+    return total / (1 << N)
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_gray_code_variant_agrees(N):
+    G = _rand(N, 309 + N)
+    idx = range(4 ** N) if N < 5 else workloads.sample_indices(N, 310, k=64)
+    idx = [int(i) for i in idx]
+    fast = np.array([_gray_code_coefficient(G, n, N) for n in idx])
+    np.testing.assert_allclose(oracle.decompose_at(G, idx), fast, rtol=0, atol=1e-13)
+
+
+def test_adjoint_dot_product():
+    """<decompose(G), y> = <G, 2^-N compose(y)> with <u, v> = sum conj(u) v."""
+    N = 3
+    G = _rand(N, 311)
+    y = workloads.gaussian_complex(3, 312).ravel()  # 64 = 4^3 values
+    lhs = np.vdot(oracle.decompose_full(G), y)
+    rhs = np.vdot(G.ravel(), oracle.compose_full(y).ravel() * 2.0 ** -N)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_gradient_of_weighted_norm_by_finite_differences():
+    """loss = sum_n w_n |c_n|^2; torch's grad_c = 2 w c; grad_G = decompose_grad(grad_c)
+    should equal dL/dRe(G) + i dL/dIm(G) (central differences)."""
+    N = 2
+    G = _rand(N, 313)
+    w = np.random.default_rng(314).uniform(size=4 ** N)
+
+    def loss(M):
+        return float(np.sum(w * np.abs(oracle.decompose_full(M)) ** 2))
+
+    grad = oracle.decompose_grad(2 * w * oracle.decompose_full(G))
+    h = 1e-6
+    for (r, q) in [(0, 0), (1, 3), (3, 2), (2, 2)]:
+        E = np.zeros_like(G)
+        E[r, q] = 1
+        d_re = (loss(G + h * E) - loss(G - h * E)) / (2 * h)
+        d_im = (loss(G + 1j * h * E) - loss(G - 1j * h * E)) / (2 * h)
+        assert abs(grad[r, q] - (d_re + 1j * d_im)) < 1e-7
+
+
+def test_rejects_bad_arguments():
+    with pytest.raises(ValueError):
+        oracle.decompose_at(np.zeros((3, 3)), [0])
+    with pytest.raises(ValueError):
+        oracle.decompose_at(np.zeros((4, 4)), [16])
+    with pytest.raises(ValueError):
+        oracle.compose_at(np.zeros(15), [0], [0])
