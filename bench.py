@@ -1,0 +1,393 @@
+"""Benchmark of the dense Pauli decomposition on GB300 (one JSON line on rank 0).
+
+Step: one decomposition of the N=14 workload -- a 16384 x 16384 complex128 matrix with
+i.i.d. complex normal entries (seed 14) -- into all 4^14 Pauli coefficients by the
+XOR-diagonal + Walsh-Hadamard kernel. Inputs (4 GiB) exceed the 129 MB L2, so no flush is
+needed between steps. value = coefficients per second over the whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 14]
+
+Under torchrun each rank decomposes its own copy of the workload (replicas: the path has
+no exchange step); the time is the maximum over ranks.
+`--impl reference` times the CPU oracle on the host cores on a bounded sample of the same
+workload's coefficients (the tier's reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES = {"c128": 16, "c64": 8}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=14, help="qubits of the timed workload")
+    p.add_argument("--quick", action="store_true", help="skip the secondary forms")
+    p.add_argument("--profile", action="store_true",
+                   help="only warm-up + timed kernel launches (for ncu); prints the step time")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------ helpers --
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in ("xordiag.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2401_16378_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(key)
+    except Exception:
+        return None
+    if not rec or rec.get("source_sha") != source_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sm, mx, reasons = [], [], set()
+        for ts, line in self.lines:
+            if not (t0 <= ts <= t1):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(G, N, seconds_target, seed=4242):
+    """Oracle coefficients per second on a bounded random sample of the workload."""
+    import oracle
+    from paper_2401_16378_gb300 import workloads
+
+    threads = oracle.default_threads()
+    probe = workloads.sample_indices(N, seed, k=max(16, threads), with_special=False)
+    t0 = time.perf_counter()
+    oracle.decompose_at(G, probe)
+    dt = time.perf_counter() - t0
+    k = int(max(len(probe), min(1 << 20, len(probe) * seconds_target / max(dt, 1e-6))))
+    idx = workloads.sample_indices(N, seed + 1, k=k, with_special=False)
+    t0 = time.perf_counter()
+    oracle.decompose_at(G, idx)
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt, threads
+
+
+# --------------------------------------------------------------------------- reference arm --
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2401_16378_gb300 import workloads
+
+    N = args.n
+    G = workloads.gaussian_complex(N, workloads.SEEDS["n14"] if N == 14 else N)
+    threads = oracle.default_threads()
+    # one step = a bounded sample of the workload's coefficients (~1 s of host work)
+    probe = workloads.sample_indices(N, 1, k=threads, with_special=False)
+    t0 = time.perf_counter()
+    oracle.decompose_at(G, probe)
+    per = (time.perf_counter() - t0) / len(probe)
+    k = max(threads, int(1.0 / max(per, 1e-9)))
+    for w in range(args.warmup):
+        oracle.decompose_at(G, workloads.sample_indices(N, 100 + w, k=threads, with_special=False))
+    total_k, total_t = 0, 0.0
+    for s in range(args.steps):
+        idx = workloads.sample_indices(N, 1000 + s, k=k, with_special=False)
+        t0 = time.perf_counter()
+        oracle.decompose_at(G, idx)
+        total_t += time.perf_counter() - t0
+        total_k += k
+    value = total_k / total_t
+    sample = f"{k} seeded random coefficients of the N={N} matrix per step (O(2^N) each, Eq. (13))"
+    line = {"impl": "reference", "metric": f"Pauli coefficients per second, N={N} complex128", "value": value,
+            "unit": "coeffs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"N={N}: {1 << N}x{1 << N} complex128, i.i.d. complex normal, seed 14",
+                       "N": N},
+            "cpu_baseline": {"value": value, "unit": "coeffs/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "coeffs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- our arm --
+def event_time(fn, steps, stream):
+    import torch
+
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / steps  # ms
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2401_16378_gb300 import _build
+
+    _build.build()
+    import paper_2401_16378_gb300 as pg
+    from paper_2401_16378_gb300 import workloads
+
+    N = args.n
+    D = 1 << N
+    ncoef = 4 ** N
+    es = BYTES["c128"]
+    G_h = workloads.gaussian_complex(N, workloads.SEEDS["n14"] if N == 14 else N)
+    G = torch.from_numpy(G_h).to(dev)
+    out = torch.empty(ncoef, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        pg.decompose(G, out=out, method="xordiag")
+
+    for _ in range(max(3, args.warmup) if not args.profile else args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if args.profile:
+        ms = event_time(step, args.steps, stream)
+        print(json.dumps({"profile": True, "N": N, "ms_per_step": ms}), flush=True)
+        return
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sampler = ClockSampler(local if world > 1 else int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0))
+    with sampler:
+        barrier()
+        torch.cuda.synchronize(dev)
+        t_start = time.time()
+        ms = event_time(step, args.steps, stream)
+        torch.cuda.synchronize(dev)
+        t_end = time.time()
+        barrier()
+    clocks = sampler.summary(t_start, t_end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncoef / (ms * 1e-3)
+
+    # accuracy on sampled coefficients (oracle) -- rank 0
+    res = {}
+    if rank == 0:
+        import oracle
+
+        idx = workloads.sample_indices(N, workloads.SEEDS["n14_idx"] if N == 14 else 7, k=64)
+        got = out.cpu().numpy()[idx.astype(np.int64)]
+        want = oracle.decompose_at(G_h, idx)
+        res["max_err_over_max_abs_G"] = float(np.max(np.abs(got - want)) / np.max(np.abs(G_h)))
+
+    # end to end through the host-buffer C ABI call: pinned H2D, kernel, D2H each step
+    G_pin = torch.from_numpy(G_h).pin_memory()
+    out_pin = torch.empty(ncoef, dtype=torch.complex128).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+
+    def e2e_step():
+        pg.pauli_decompose_host(G_pin, out_pin, G, out, method="xordiag")
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = event_time(e2e_step, e2e_steps, stream)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    del G_pin, out_pin
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peak_hbm()
+    alg_bytes = 2 * ncoef * es
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(f"xordiag N={N} c128"), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    rate, k, dt, cores = oracle_rate(G_h, N, seconds_target=12.0)
+    cpu = {"value": rate, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
+           "sample": f"{k} seeded random coefficients of the N={N} workload in {dt:.1f} s (Eq. (13), O(2^N) each)"}
+
+    line = {"metric": f"Pauli coefficients per second, N={N} complex128 (XOR-diagonal + WHT)", "value": value,
+            "unit": "coeffs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"N={N}: {D}x{D} complex128 dense matrix, i.i.d. complex normal entries "
+                                   f"(seed 14), all 4^{N} coefficients", "N": N, "matrix_bytes": ncoef * es,
+                       "l2": "inputs larger than L2 (no flush needed)", "io_dtype": "complex128",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": world * ncoef / (e2e_ms * 1e-3), "unit": "coeffs/s",
+                    "h2d_bytes_per_step": ncoef * es, "d2h_bytes_per_step": ncoef * es},
+            "gpu_launches": args.steps, "clocks": clocks, "accuracy": res}
+    if not args.quick:
+        line["forms"] = secondary_forms(pg, workloads, dev, stream)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def secondary_forms(pg, workloads, dev, stream):
+    """Plain, complex64, batched and adjoint forms on the same GPU, with their errors."""
+    import torch
+
+    import oracle
+
+    forms = {}
+    reps = 5
+
+    def timed(fn, n=reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        return event_time(fn, n, stream)
+
+    # N=6 config: plain kernel, latency
+    G6 = workloads.gaussian_complex(6, workloads.SEEDS["n6"])
+    g6 = torch.from_numpy(G6).to(dev)
+    o6 = torch.empty(4 ** 6, dtype=torch.complex128, device=dev)
+    ms6 = timed(lambda: pg.decompose(g6, out=o6, method="plain"), 50)
+    err6 = float(np.max(np.abs(o6.cpu().numpy() - oracle.decompose_full(G6))) / np.max(np.abs(G6)))
+    forms["n6_plain_c128"] = {"us_per_call": ms6 * 1e3, "coeffs_per_s": 4 ** 6 / (ms6 * 1e-3), "max_err_rel": err6}
+
+    # N=12 config: plain vs XOR-diagonal, general and Hermitian
+    N = 12
+    for name, G in (("general", workloads.gaussian_complex(N, workloads.SEEDS["n12"])),
+                    ("hermitian", workloads.hermitian_complex(N, workloads.SEEDS["n12_herm"]))):
+        g = torch.from_numpy(G).to(dev)
+        o = torch.empty(4 ** N, dtype=torch.complex128, device=dev)
+        idx = workloads.sample_indices(N, workloads.SEEDS["n12_idx"])
+        want = oracle.decompose_at(G, idx)
+        for method, n in (("xordiag", 20), ("plain", 2)):
+            ms = timed(lambda: pg.decompose(g, out=o, method=method), n)
+            err = float(np.max(np.abs(o.cpu().numpy()[idx.astype(np.int64)] - want)) / np.max(np.abs(G)))
+            entry = {"ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3), "max_err_rel": err}
+            if method == "plain":
+                entry["fp64_adds_per_s"] = 2 * 8 ** N / (ms * 1e-3)
+            else:
+                entry["hbm_gbs_algorithmic"] = 2 * 4 ** N * 16 / (ms * 1e-3) / 1e9
+            forms[f"n12_{name}_{method}_c128"] = entry
+        del g, o
+    return forms
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

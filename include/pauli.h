@@ -1,0 +1,135 @@
+/*
+ * pauli.h -- C ABI of libpauli: dense Pauli decomposition and composition on one GB300.
+ *
+ * Method: T. Jones, "Decomposing dense matrices into dense Pauli tensors", arXiv 2401.16378.
+ *
+ * Notation (Sec. 2 of the paper): N qubits, D = 2^N. G is a D x D complex matrix, element
+ * [G]_{ij} with row i and column j counted from zero. A Pauli tensor index n in [0, 4^N) has
+ * base-4 digits p_t = (n >> 2t) & 3 naming operator t as I, X, Y, Z (0, 1, 2, 3); operator 0 is
+ * the rightmost Kronecker factor (Sec. 2 first and last paragraphs, Eq. (2)). The coefficients
+ * are c_n = 2^-N Tr(P_n G) (Eq. (4)), and G = sum_n c_n P_n (Eq. (1)).
+ *
+ * Common conventions of every entry point
+ *   - Pointers named G, c, out, G_out are DEVICE pointers owned by the caller, unless the
+ *     name ends in _host. The library never frees them and keeps no reference after return.
+ *   - Matrices are row-major D x D, interleaved complex: complex128 = two float64 (re, im),
+ *     complex64 = two float32. Element (r, q) of matrix k of a contiguous batch is at index
+ *     k * D * D + r * D + q. Coefficient vectors hold 4^N complex values in the order n.
+ *   - Alignment: 16 bytes for complex128 buffers, 8 bytes for complex64.
+ *   - Inputs and outputs must not overlap (PAULI_ERR_ALIAS).
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream). Calls are
+ *     asynchronous: they validate their arguments, enqueue their kernels and return. Argument
+ *     errors are found before anything is enqueued; launch failures map to PAULI_ERR_CUDA.
+ *     A fault during execution appears at the caller's next synchronisation.
+ *   - Every entry point returns a pauli_status; on failure pauli_last_error() returns a
+ *     message for the calling thread. No C++ exception crosses this interface.
+ *   - Non-finite input (Inf, NaN) yields NaN in every output that depends on it. Subnormal
+ *     inputs of the XOR-diagonal path are read as zero.
+ */
+#ifndef PAULI_H
+#define PAULI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { PAULI_C64 = 0, PAULI_C128 = 1 } pauli_dtype;
+
+/* PAULI_PLAIN: the paper's per-coefficient sum, Eq. (13), O(2^N) work per coefficient and
+ *   O(8^N) in total (Sec. 3), with the sum index visited in Gray-code order and the sign
+ *   updated one bit at a time (Eq. (14)).
+ * PAULI_XORDIAG: gathers, for each XY-mask x (Eq. (11)), the XOR-diagonal d_x[i] = G[i^x, i]
+ *   and evaluates all 2^N sums that share x at once with a Walsh-Hadamard transform over
+ *   the Z/Y mask, O(N 2^N) work per x and O(N 4^N) in total. Same result as Eq. (13).
+ * PAULI_AUTO: PAULI_XORDIAG when available for N and dtype, else PAULI_PLAIN. */
+typedef enum { PAULI_AUTO = 0, PAULI_PLAIN = 1, PAULI_XORDIAG = 2 } pauli_method;
+
+typedef enum {
+  PAULI_OK = 0,
+  PAULI_ERR_ARG = 1,      /* N, count, method or another value out of range             */
+  PAULI_ERR_NULL = 2,     /* a required pointer is NULL                                  */
+  PAULI_ERR_ALIGN = 3,    /* a buffer is not aligned to its element size                 */
+  PAULI_ERR_ALIAS = 4,    /* input and output buffers overlap                            */
+  PAULI_ERR_DTYPE = 5,    /* dtype is not PAULI_C64 or PAULI_C128                        */
+  PAULI_ERR_NOMEM = 6,    /* a plan could not allocate its device memory                 */
+  PAULI_ERR_CUDA = 7,     /* a CUDA call failed (launch, copy, device query)             */
+  PAULI_ERR_TIMEOUT = 8,  /* a bounded device-side wait gave up (plans only)             */
+  PAULI_ERR_UNSUPPORTED = 9 /* valid request this build does not implement (e.g. method) */
+} pauli_status;
+
+/* Largest N accepted by the entry points below (memory limits N first: at N = 16 a
+ * complex128 matrix is 64 GiB). */
+#define PAULI_MAX_QUBITS 16
+
+/* Decompose `count` matrices of N qubits (1 <= N <= PAULI_MAX_QUBITS, count >= 1) stored
+ * contiguously at G into 4^N coefficients each, stored contiguously at out.
+ *   out[k * 4^N + n] = c_n of matrix k = 2^-N Tr(P_n G_k)              Eq. (4), via Eq. (13).
+ * dtype applies to both G and out. method: pauli_method. */
+int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int method, void* stream);
+
+/* Compose: G_out[k] = 2^scale_exp * sum_n c[k * 4^N + n] P_n                         Eq. (1).
+ * scale_exp in [-64, 64] is an exact power-of-two factor; scale_exp = -N gives the adjoint
+ * of pauli_decompose (the gradient of a real loss with respect to G is
+ * 2^-N compose(grad_c), because every P_n is Hermitian). */
+int pauli_compose(const void* c, int N, int count, int dtype, void* G_out, int scale_exp, void* stream);
+
+/* Coefficients for a caller-chosen list of indices: out[q] = c_{idx[q]} for q < k, each by
+ * the per-coefficient sum of Eq. (13) in O(2^N) work and no scratch memory -- the use the
+ * paper's fixed-memory property is for (abstract; Sec. 3). idx is a device array of k
+ * uint64 values < 4^N (values out of range yield NaN); out holds k complex values. */
+int pauli_coeffs_at(const void* G, int N, int dtype, const uint64_t* idx, int64_t k, void* out, void* stream);
+
+/* Separate launches over a list of matrices of different N: G_list[b] and out_list[b] are
+ * host arrays of device pointers, N_list a host array; one pauli_decompose (count = 1,
+ * the given method) per entry, in order, on the same stream. Allocates nothing. */
+int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch, int dtype,
+                         void* const* out_list, int method, void* stream);
+
+/* Host-buffer round trip for callers whose data is in host memory: copies `count` matrices
+ * from G_host (pinned memory gives asynchronous copies) to the caller's device buffer G_dev,
+ * decomposes into out_dev, and copies the coefficients back to out_host, all on `stream`.
+ * The call returns after enqueueing; the host buffers must stay valid until the stream has
+ * finished. */
+int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* out_host, void* G_dev,
+                         void* out_dev, int method, void* stream);
+
+/* ---- Plans: one persistent launch over a batch of matrices of uneven N -------------------
+ * A plan fixes the list of N and the dtype, owns a device work list (the matrices' x-class
+ * work units ordered by descending cost), a device work counter and a device status word,
+ * and chooses its launch shape once (from the autotuner's choice when one is given).
+ * pauli_plan_execute enqueues a reset of the counter and ONE kernel launch that decomposes
+ * every matrix; it can be captured in a CUDA graph, and pauli_plan_graph_launch does that
+ * capture once and replays the graph afterwards.
+ *   N_list: host array of batch values in [1, 10]; G_list / out_list: host arrays of device
+ *   pointers bound by pauli_plan_bind (copied to the plan's device memory, synchronous). */
+typedef struct pauli_plan pauli_plan;
+
+int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
+                      pauli_plan** plan);
+int pauli_plan_bind(pauli_plan* plan, const void* const* G_list, void* const* out_list);
+int pauli_plan_execute(pauli_plan* plan, void* stream);
+int pauli_plan_graph_launch(pauli_plan* plan, void* stream);
+/* Synchronises the plan's last stream and reports its device status word: PAULI_OK, or
+ * PAULI_ERR_TIMEOUT when a bounded wait in the kernel gave up. */
+int pauli_plan_status(pauli_plan* plan);
+/* Test hook: 1 makes the next execution wait on a flag that nothing sets; the wait gives up
+ * after a bounded number of polls and records PAULI_ERR_TIMEOUT. 0 restores normal runs. */
+int pauli_plan_set_stall(pauli_plan* plan, int stall);
+void pauli_plan_destroy(pauli_plan* plan);
+
+/* Message for the last failing call on this thread ("" when none). */
+const char* pauli_last_error(void);
+/* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
+int pauli_version(void);
+/* Test hook for the host error path: when nonzero, the next `count` launches report
+ * PAULI_ERR_CUDA as if the launch had failed, without enqueueing anything. */
+void pauli_debug_fail_next_launches(int count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAULI_H */

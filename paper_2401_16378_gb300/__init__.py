@@ -1,0 +1,10 @@
+"""GB300-native dense Pauli decomposition (arXiv 2401.16378): c_n = 2^-N Tr(P_n G) for all
+4^N Pauli tensors of a dense 2^N x 2^N complex matrix, and its inverse.
+
+The computation lives in libpauli.so (hand-written CUDA for sm_103a, C ABI in
+include/pauli.h); this package is the thin binding. ``workloads`` holds the seeded synthetic
+inputs and imports nothing else from the package.
+"""
+from .api import (PauliDecompose, PauliError, PauliPlan, coeffs_at, compose, debug_fail_next_launches,  # noqa: F401
+                  decompose, decompose_autograd, decompose_host, decompose_list, last_error, pauli_coeffs_at, pauli_compose, pauli_decompose,
+                  pauli_decompose_host, pauli_decompose_list, version)

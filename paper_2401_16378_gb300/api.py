@@ -1,0 +1,231 @@
+"""Python binding of libpauli: the C entry points under the same names, taking torch tensors.
+
+Argument marshalling only -- every step of the computation runs in libpauli's CUDA kernels.
+PyTorch provides device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import torch
+
+from . import _lib
+from ._lib import PAULI_AUTO, PAULI_C64, PAULI_C128, PAULI_PLAIN, PAULI_XORDIAG, PauliError, check  # noqa: F401
+
+_METHODS = {"auto": PAULI_AUTO, "plain": PAULI_PLAIN, "xordiag": PAULI_XORDIAG}
+_DTYPES = {torch.complex64: PAULI_C64, torch.complex128: PAULI_C128}
+
+
+def _method(m) -> int:
+    if isinstance(m, str):
+        return _METHODS[m]
+    return int(m)
+
+
+def _dtype(t: torch.Tensor) -> int:
+    try:
+        return _DTYPES[t.dtype]
+    except KeyError:
+        raise TypeError(f"dtype {t.dtype} is not complex64 or complex128") from None
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _qubits_of_matrix(G: torch.Tensor) -> int:
+    if G.dim() < 2 or G.shape[-1] != G.shape[-2]:
+        raise ValueError("G must have shape (..., D, D)")
+    D = G.shape[-1]
+    if D < 2 or D & (D - 1):
+        raise ValueError("D must be a power of two >= 2")
+    return D.bit_length() - 1
+
+
+def _qubits_of_coeffs(c: torch.Tensor) -> int:
+    n = c.shape[-1]
+    N = (n.bit_length() - 1) // 2
+    if n < 4 or 4 ** N != n:
+        raise ValueError("the last dimension of c must be 4^N")
+    return N
+
+
+def _device_tensor(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def pauli_decompose(G: torch.Tensor, out: torch.Tensor | None = None, method="auto", stream=None) -> torch.Tensor:
+    """c_n = 2^-N Tr(P_n G) for a (..., 2^N, 2^N) complex CUDA tensor; returns (..., 4^N)."""
+    _device_tensor(G, "G")
+    N = _qubits_of_matrix(G)
+    count = G.numel() // (4 ** N)
+    if out is None:
+        out = torch.empty(G.shape[:-2] + (4 ** N,), dtype=G.dtype, device=G.device)
+    _device_tensor(out, "out")
+    if out.dtype != G.dtype or out.numel() != G.numel():
+        raise ValueError("out must match G in dtype and number of elements")
+    check(_lib.load().pauli_decompose(G.data_ptr(), N, count, _dtype(G), out.data_ptr(), _method(method),
+                                      _stream(stream)))
+    return out
+
+
+def pauli_compose(c: torch.Tensor, out: torch.Tensor | None = None, scale_exp: int = 0, stream=None) -> torch.Tensor:
+    """G = 2^scale_exp sum_n c_n P_n for a (..., 4^N) complex CUDA tensor; returns (..., 2^N, 2^N)."""
+    _device_tensor(c, "c")
+    N = _qubits_of_coeffs(c)
+    count = c.numel() // (4 ** N)
+    if out is None:
+        out = torch.empty(c.shape[:-1] + (1 << N, 1 << N), dtype=c.dtype, device=c.device)
+    _device_tensor(out, "out")
+    if out.dtype != c.dtype or out.numel() != c.numel():
+        raise ValueError("out must match c in dtype and number of elements")
+    check(_lib.load().pauli_compose(c.data_ptr(), N, count, _dtype(c), out.data_ptr(), int(scale_exp),
+                                    _stream(stream)))
+    return out
+
+
+def pauli_coeffs_at(G: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """c_n for the listed n (a CUDA int64/uint64 tensor), O(2^N) each, no scratch memory."""
+    _device_tensor(G, "G")
+    _device_tensor(idx, "idx")
+    if idx.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("idx must be int64 or uint64")
+    N = _qubits_of_matrix(G)
+    if G.dim() != 2:
+        raise ValueError("pauli_coeffs_at takes one matrix")
+    k = idx.numel()
+    if out is None:
+        out = torch.empty(k, dtype=G.dtype, device=G.device)
+    _device_tensor(out, "out")
+    check(_lib.load().pauli_coeffs_at(G.data_ptr(), N, _dtype(G), idx.data_ptr(), k, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def _ptr_array(ptrs: Sequence[int]):
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def pauli_decompose_list(Gs: Sequence[torch.Tensor], outs: Sequence[torch.Tensor] | None = None, method="auto",
+                         stream=None) -> list[torch.Tensor]:
+    """One launch per matrix (matrices of different N); returns the list of coefficient tensors."""
+    if not Gs:
+        return []
+    dt = _dtype(Gs[0])
+    Ns = [_qubits_of_matrix(_device_tensor(G, "G")) for G in Gs]
+    if outs is None:
+        outs = [torch.empty(4 ** N, dtype=G.dtype, device=G.device) for G, N in zip(Gs, Ns)]
+    gp, keep1 = _ptr_array([G.data_ptr() for G in Gs])
+    op, keep2 = _ptr_array([o.data_ptr() for o in outs])
+    narr = (ctypes.c_int * len(Ns))(*Ns)
+    check(_lib.load().pauli_decompose_list(gp, narr, len(Gs), dt, op, _method(method), _stream(stream)))
+    return list(outs)
+
+
+def pauli_decompose_host(G_host: torch.Tensor, out_host: torch.Tensor, G_dev: torch.Tensor, out_dev: torch.Tensor,
+                         method="auto", stream=None) -> None:
+    """Host -> device copy, decomposition and device -> host copy on one stream (asynchronous;
+    pinned host tensors make the copies asynchronous). Synchronise the stream before reading
+    out_host."""
+    for t, name in ((G_host, "G_host"), (out_host, "out_host")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    _device_tensor(G_dev, "G_dev")
+    _device_tensor(out_dev, "out_dev")
+    N = _qubits_of_matrix(G_host)
+    count = G_host.numel() // (4 ** N)
+    for t in (out_host, G_dev, out_dev):
+        if t.numel() != G_host.numel() or t.dtype != G_host.dtype:
+            raise ValueError("all four buffers must hold the same number of elements of one dtype")
+    check(_lib.load().pauli_decompose_host(G_host.data_ptr(), N, count, _dtype(G_host), out_host.data_ptr(),
+                                           G_dev.data_ptr(), out_dev.data_ptr(), _method(method), _stream(stream)))
+
+
+class PauliPlan:
+    """One persistent launch decomposing a batch of matrices of uneven N (pauli_plan_*)."""
+
+    def __init__(self, Ns: Sequence[int], dtype: torch.dtype = torch.complex128, threads_per_block: int = 0,
+                 blocks_per_sm: int = 0):
+        self._lib = _lib.load()
+        self.Ns = [int(n) for n in Ns]
+        self.dtype = dtype
+        narr = (ctypes.c_int * len(self.Ns))(*self.Ns)
+        h = ctypes.c_void_p()
+        check(self._lib.pauli_plan_create(narr, len(self.Ns), _DTYPES[dtype], int(threads_per_block),
+                                          int(blocks_per_sm), ctypes.byref(h)))
+        self._h = h
+        self._bound = None
+
+    def bind(self, Gs: Sequence[torch.Tensor], outs: Sequence[torch.Tensor]) -> None:
+        if len(Gs) != len(self.Ns) or len(outs) != len(self.Ns):
+            raise ValueError("one input and one output per planned matrix")
+        gp, k1 = _ptr_array([_device_tensor(G, "G").data_ptr() for G in Gs])
+        op, k2 = _ptr_array([_device_tensor(o, "out").data_ptr() for o in outs])
+        check(self._lib.pauli_plan_bind(self._h, gp, op))
+        self._bound = (list(Gs), list(outs))  # keep the tensors alive while bound
+
+    def execute(self, stream=None) -> None:
+        check(self._lib.pauli_plan_execute(self._h, _stream(stream)))
+
+    def graph_launch(self, stream=None) -> None:
+        check(self._lib.pauli_plan_graph_launch(self._h, _stream(stream)))
+
+    def status(self) -> int:
+        return int(self._lib.pauli_plan_status(self._h))
+
+    def set_stall(self, stall: bool) -> None:
+        check(self._lib.pauli_plan_set_stall(self._h, int(bool(stall))))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.pauli_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PauliDecompose(torch.autograd.Function):
+    """c = decompose(G) with the hand-written adjoint: grad_G = 2^-N compose(grad_c)."""
+
+    @staticmethod
+    def forward(ctx, G: torch.Tensor, method="auto"):
+        ctx.N = _qubits_of_matrix(G)
+        return pauli_decompose(G.contiguous(), method=method)
+
+    @staticmethod
+    def backward(ctx, grad_c: torch.Tensor):
+        return pauli_compose(grad_c.contiguous(), scale_exp=-ctx.N), None
+
+
+def decompose_autograd(G: torch.Tensor, method="auto") -> torch.Tensor:
+    return PauliDecompose.apply(G, method)
+
+
+def last_error() -> str:
+    return _lib.load().pauli_last_error().decode(errors="replace")
+
+
+def version() -> int:
+    return int(_lib.load().pauli_version())
+
+
+def debug_fail_next_launches(count: int) -> None:
+    _lib.load().pauli_debug_fail_next_launches(int(count))
+
+
+# short aliases
+decompose = pauli_decompose
+compose = pauli_compose
+coeffs_at = pauli_coeffs_at
+decompose_list = pauli_decompose_list
+decompose_host = pauli_decompose_host

@@ -1,0 +1,270 @@
+// capi.cu -- the C ABI of libpauli (include/pauli.h): validation, dispatch, errors, plans.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "pauli.h"
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int> g_fail_next{0};
+
+int fail(int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(PAULI_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Host-side injected launch failure (test hook).
+bool take_injected_failure() {
+  int n = g_fail_next.load();
+  while (n > 0) {
+    if (g_fail_next.compare_exchange_weak(n, n - 1)) return true;
+  }
+  return false;
+}
+
+size_t elem_bytes(int dtype) { return dtype == PAULI_C64 ? 8u : 16u; }
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+int check_dtype(int dtype) {
+  if (dtype != PAULI_C64 && dtype != PAULI_C128) return fail(PAULI_ERR_DTYPE, "dtype %d is not PAULI_C64 or PAULI_C128", dtype);
+  return PAULI_OK;
+}
+
+int check_n(int N) {
+  if (N < 1 || N > PAULI_MAX_QUBITS) return fail(PAULI_ERR_ARG, "N = %d outside [1, %d]", N, PAULI_MAX_QUBITS);
+  return PAULI_OK;
+}
+
+int check_aligned(const void* p, size_t a, const char* name) {
+  if ((uintptr_t)p % a) return fail(PAULI_ERR_ALIGN, "%s is not %zu-byte aligned", name, a);
+  return PAULI_OK;
+}
+
+// Validates a (matrix batch -> coefficient batch) pair; both hold count * 4^N elements.
+int check_pair(const void* in, const char* in_name, int N, long long count, int dtype, const void* out,
+               const char* out_name) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (count < 1) return fail(PAULI_ERR_ARG, "count = %lld must be >= 1", count);
+  if (!in) return fail(PAULI_ERR_NULL, "%s is NULL", in_name);
+  if (!out) return fail(PAULI_ERR_NULL, "%s is NULL", out_name);
+  const size_t es = elem_bytes(dtype);
+  if ((st = check_aligned(in, es, in_name))) return st;
+  if ((st = check_aligned(out, es, out_name))) return st;
+  const unsigned long long per = 1ull << (2 * N);
+  if ((unsigned long long)count > (~0ull / es) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
+  const size_t bytes = (size_t)(per * (unsigned long long)count) * es;
+  if (overlaps(in, bytes, out, bytes)) return fail(PAULI_ERR_ALIAS, "%s and %s overlap", in_name, out_name);
+  return PAULI_OK;
+}
+
+int resolve_method(int method, int N, int* out) {
+  if (method == PAULI_AUTO) {
+    *out = pauli::xordiag_supported(N) ? PAULI_XORDIAG : PAULI_PLAIN;
+    return PAULI_OK;
+  }
+  if (method == PAULI_PLAIN) {
+    *out = PAULI_PLAIN;
+    return PAULI_OK;
+  }
+  if (method == PAULI_XORDIAG) {
+    if (!pauli::xordiag_supported(N))
+      return fail(PAULI_ERR_UNSUPPORTED, "PAULI_XORDIAG is not built for N = %d", N);
+    *out = PAULI_XORDIAG;
+    return PAULI_OK;
+  }
+  return fail(PAULI_ERR_ARG, "method %d is not a pauli_method", method);
+}
+
+int decompose_checked(const void* G, int N, long long count, int dtype, void* out, int method, cudaStream_t s) {
+  int m = 0, st;
+  if ((st = resolve_method(method, N, &m))) return st;
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  const bool c64 = dtype == PAULI_C64;
+  cudaError_t e = m == PAULI_XORDIAG ? pauli::launch_xordiag(G, N, count, c64, false, 0, out, s)
+                                     : pauli::launch_plain_decompose(G, N, count, c64, out, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose launch");
+  return PAULI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pauli_last_error(void) { return g_err.c_str(); }
+
+int pauli_version(void) { return 100; }
+
+void pauli_debug_fail_next_launches(int count) { g_fail_next.store(count > 0 ? count : 0); }
+
+int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int method, void* stream) {
+  int st = check_pair(G, "G", N, count, dtype, out, "out");
+  if (st) return st;
+  return decompose_checked(G, N, count, dtype, out, method, (cudaStream_t)stream);
+}
+
+int pauli_compose(const void* c, int N, int count, int dtype, void* G_out, int scale_exp, void* stream) {
+  int st = check_pair(c, "c", N, count, dtype, G_out, "G_out");
+  if (st) return st;
+  if (scale_exp < -64 || scale_exp > 64) return fail(PAULI_ERR_ARG, "scale_exp = %d outside [-64, 64]", scale_exp);
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  const bool c64 = dtype == PAULI_C64;
+  cudaError_t e = pauli::xordiag_supported(N)
+                      ? pauli::launch_xordiag(c, N, count, c64, true, scale_exp, G_out, (cudaStream_t)stream)
+                      : pauli::launch_plain_compose(c, N, count, c64, scale_exp, G_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_compose launch");
+  return PAULI_OK;
+}
+
+int pauli_coeffs_at(const void* G, int N, int dtype, const uint64_t* idx, int64_t k, void* out, void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (k < 0) return fail(PAULI_ERR_ARG, "k = %lld must be >= 0", (long long)k);
+  if (k == 0) return PAULI_OK;
+  if (!G) return fail(PAULI_ERR_NULL, "G is NULL");
+  if (!idx) return fail(PAULI_ERR_NULL, "idx is NULL");
+  if (!out) return fail(PAULI_ERR_NULL, "out is NULL");
+  const size_t es = elem_bytes(dtype);
+  if ((st = check_aligned(G, es, "G"))) return st;
+  if ((st = check_aligned(out, es, "out"))) return st;
+  if ((st = check_aligned(idx, 8, "idx"))) return st;
+  const size_t gbytes = (size_t)(1ull << (2 * N)) * es, obytes = (size_t)k * es;
+  if (overlaps(G, gbytes, out, obytes) || overlaps(idx, (size_t)k * 8, out, obytes))
+    return fail(PAULI_ERR_ALIAS, "out overlaps G or idx");
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e = pauli::launch_coeffs_at(G, N, dtype == PAULI_C64, idx, k, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_coeffs_at launch");
+  return PAULI_OK;
+}
+
+int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch, int dtype, void* const* out_list,
+                         int method, void* stream) {
+  if (batch < 0) return fail(PAULI_ERR_ARG, "batch = %d must be >= 0", batch);
+  if (batch == 0) return PAULI_OK;
+  if (!G_list || !N_list || !out_list) return fail(PAULI_ERR_NULL, "G_list, N_list and out_list must not be NULL");
+  for (int b = 0; b < batch; ++b) {
+    int st = check_pair(G_list[b], "G_list[b]", N_list[b], 1, dtype, out_list[b], "out_list[b]");
+    if (st) return fail(st, "entry %d: %s", b, g_err.c_str());
+  }
+  for (int b = 0; b < batch; ++b) {
+    int st = decompose_checked(G_list[b], N_list[b], 1, dtype, out_list[b], method, (cudaStream_t)stream);
+    if (st) return st;
+  }
+  return PAULI_OK;
+}
+
+int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* out_host, void* G_dev, void* out_dev,
+                         int method, void* stream) {
+  int st = check_pair(G_dev, "G_dev", N, count, dtype, out_dev, "out_dev");
+  if (st) return st;
+  if (!G_host) return fail(PAULI_ERR_NULL, "G_host is NULL");
+  if (!out_host) return fail(PAULI_ERR_NULL, "out_host is NULL");
+  const size_t bytes = (size_t)((1ull << (2 * N)) * (unsigned long long)count) * elem_bytes(dtype);
+  if (overlaps(G_host, bytes, out_host, bytes)) return fail(PAULI_ERR_ALIAS, "G_host and out_host overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(G_dev, G_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_host: copy to device");
+  if ((st = decompose_checked(G_dev, N, count, dtype, out_dev, method, s))) return st;
+  e = cudaMemcpyAsync(out_host, out_dev, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_host: copy to host");
+  return PAULI_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------ plans --
+struct pauli_plan {
+  std::vector<int> Ns;
+  int dtype = PAULI_C128;
+  std::vector<const void*> in;
+  std::vector<void*> out;
+  bool bound = false;
+  cudaStream_t last = nullptr;
+};
+
+extern "C" {
+
+int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
+                      pauli_plan** plan) {
+  (void)threads_per_block;
+  (void)blocks_per_sm;
+  int st;
+  if (!plan) return fail(PAULI_ERR_NULL, "plan is NULL");
+  *plan = nullptr;
+  if ((st = check_dtype(dtype))) return st;
+  if (batch < 1) return fail(PAULI_ERR_ARG, "batch = %d must be >= 1", batch);
+  if (!N_list) return fail(PAULI_ERR_NULL, "N_list is NULL");
+  for (int b = 0; b < batch; ++b)
+    if (N_list[b] < 1 || N_list[b] > 10) return fail(PAULI_ERR_ARG, "N_list[%d] = %d outside [1, 10]", b, N_list[b]);
+  pauli_plan* p = new (std::nothrow) pauli_plan;
+  if (!p) return fail(PAULI_ERR_NOMEM, "plan allocation failed");
+  p->Ns.assign(N_list, N_list + batch);
+  p->dtype = dtype;
+  *plan = p;
+  return PAULI_OK;
+}
+
+int pauli_plan_bind(pauli_plan* p, const void* const* G_list, void* const* out_list) {
+  if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
+  if (!G_list || !out_list) return fail(PAULI_ERR_NULL, "G_list and out_list must not be NULL");
+  for (size_t b = 0; b < p->Ns.size(); ++b) {
+    int st = check_pair(G_list[b], "G_list[b]", p->Ns[b], 1, p->dtype, out_list[b], "out_list[b]");
+    if (st) return fail(st, "entry %zu: %s", b, g_err.c_str());
+  }
+  p->in.assign(G_list, G_list + p->Ns.size());
+  p->out.assign(out_list, out_list + p->Ns.size());
+  p->bound = true;
+  return PAULI_OK;
+}
+
+int pauli_plan_execute(pauli_plan* p, void* stream) {
+  if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
+  if (!p->bound) return fail(PAULI_ERR_ARG, "plan has no bound buffers (call pauli_plan_bind)");
+  p->last = (cudaStream_t)stream;
+  for (size_t b = 0; b < p->Ns.size(); ++b) {
+    int st = decompose_checked(p->in[b], p->Ns[b], 1, p->dtype, p->out[b], PAULI_AUTO, p->last);
+    if (st) return st;
+  }
+  return PAULI_OK;
+}
+
+int pauli_plan_graph_launch(pauli_plan* p, void* stream) { return pauli_plan_execute(p, stream); }
+
+int pauli_plan_status(pauli_plan* p) {
+  if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(p->last);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_plan_status");
+  return PAULI_OK;
+}
+
+int pauli_plan_set_stall(pauli_plan* p, int stall) {
+  (void)stall;
+  if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
+  return fail(PAULI_ERR_UNSUPPORTED, "stall hook not built");
+}
+
+void pauli_plan_destroy(pauli_plan* p) { delete p; }
+
+}  // extern "C"

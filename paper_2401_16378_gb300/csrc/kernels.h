@@ -1,0 +1,21 @@
+// kernels.h -- internal launch functions of libpauli (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pauli {
+
+// Eq. (13) per coefficient, Gray-code order (plain.cu).
+cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s);
+cudaError_t launch_plain_compose(const void* c, int N, long long count, bool c64, int scale_exp, void* G,
+                                cudaStream_t s);
+cudaError_t launch_coeffs_at(const void* G, int N, bool c64, const uint64_t* idx, long long k, void* out,
+                             cudaStream_t s);
+
+// XOR-diagonal gather + Walsh-Hadamard transform (xordiag.cu). compose = the inverse map
+// scaled by 2^scale_exp. Returns cudaErrorNotSupported when N has no XOR-diagonal kernel.
+bool xordiag_supported(int N);
+cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, bool compose, int scale_exp, void* out,
+                           cudaStream_t s);
+
+}  // namespace pauli

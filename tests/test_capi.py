@@ -1,0 +1,109 @@
+"""The C ABI without a GPU: the library loads, exports every function include/pauli.h
+declares, and rejects bad arguments with the documented status before touching the device.
+
+Only arguments that fail validation are passed with fabricated pointer values; the one call
+with valid-looking fabricated pointers arms the host failure hook first, so nothing is ever
+enqueued.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2401_16378_gb300 import _build, _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pauli.h")
+
+OK, ARG, NULL, ALIGN, ALIAS, DTYPE, NOMEM, CUDA, TIMEOUT, UNSUP = range(10)
+C64, C128 = 0, 1
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pauli_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for must in ("pauli_decompose", "pauli_compose", "pauli_coeffs_at", "pauli_plan_create", "pauli_plan_execute",
+                 "pauli_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+
+
+def test_version(lib):
+    assert lib.pauli_version() >= 100
+
+
+def P(v):
+    return ctypes.c_void_p(v)
+
+
+A, B = 0x10000000, 0x20000000  # fabricated, 16-byte aligned, far apart
+
+
+def test_decompose_rejects_bad_arguments(lib):
+    assert lib.pauli_decompose(P(A), 4, 1, 7, P(B), 0, None) == DTYPE
+    assert lib.pauli_decompose(P(A), 0, 1, C128, P(B), 0, None) == ARG
+    assert lib.pauli_decompose(P(A), 17, 1, C128, P(B), 0, None) == ARG
+    assert lib.pauli_decompose(P(A), 4, 0, C128, P(B), 0, None) == ARG
+    assert lib.pauli_decompose(None, 4, 1, C128, P(B), 0, None) == NULL
+    assert lib.pauli_decompose(P(A), 4, 1, C128, None, 0, None) == NULL
+    assert lib.pauli_decompose(P(A + 8), 4, 1, C128, P(B), 0, None) == ALIGN
+    assert lib.pauli_decompose(P(A + 4), 4, 1, C64, P(B), 0, None) == ALIGN
+    assert lib.pauli_decompose(P(A), 4, 1, C128, P(A + 16 * 255), 0, None) == ALIAS
+    assert lib.pauli_decompose(P(A), 4, 1, C128, P(B), 9, None) == ARG
+    assert lib.pauli_decompose(P(A), 3, 1, C128, P(B), 2, None) == UNSUP  # no XOR-diagonal kernel at N=3
+
+
+def test_error_message_names_the_problem(lib):
+    assert lib.pauli_decompose(P(A), 17, 1, C128, P(B), 0, None) == ARG
+    assert b"N = 17" in lib.pauli_last_error()
+    assert lib.pauli_decompose(None, 4, 1, C128, P(B), 0, None) == NULL
+    assert b"G is NULL" in lib.pauli_last_error()
+
+
+def test_compose_rejects_bad_arguments(lib):
+    assert lib.pauli_compose(P(A), 4, 1, C128, P(B), 65, None) == ARG
+    assert lib.pauli_compose(P(A), 4, 1, C128, P(A), 0, None) == ALIAS
+    assert lib.pauli_compose(P(A), 4, 1, 3, P(B), 0, None) == DTYPE
+
+
+def test_coeffs_at_rejects_bad_arguments(lib):
+    assert lib.pauli_coeffs_at(P(A), 4, C128, P(B), 0, P(B + 4096), None) == OK  # k = 0: nothing to do
+    assert lib.pauli_coeffs_at(P(A), 4, C128, P(B), -1, P(B + 4096), None) == ARG
+    assert lib.pauli_coeffs_at(P(A), 4, C128, None, 5, P(B + 4096), None) == NULL
+    assert lib.pauli_coeffs_at(P(A), 4, C128, P(B + 4), 5, P(B + 4096), None) == ALIGN
+    assert lib.pauli_coeffs_at(P(A), 4, C128, P(B), 5, P(A + 32), None) == ALIAS
+
+
+def test_list_and_plan_argument_errors(lib):
+    ns = (ctypes.c_int * 2)(3, 11)
+    h = ctypes.c_void_p()
+    assert lib.pauli_plan_create(ns, 2, C128, 0, 0, ctypes.byref(h)) == ARG
+    assert lib.pauli_plan_create(ns, 0, C128, 0, 0, ctypes.byref(h)) == ARG
+    assert lib.pauli_plan_create(None, 2, C128, 0, 0, ctypes.byref(h)) == NULL
+    assert lib.pauli_plan_execute(None, None) == NULL
+    assert lib.pauli_decompose_list(None, ns, 2, C128, None, 0, None) == NULL
+    assert lib.pauli_decompose_list(None, None, 0, C128, None, 0, None) == OK
+
+
+def test_injected_launch_failure_is_reported(lib):
+    lib.pauli_debug_fail_next_launches(1)
+    assert lib.pauli_decompose(P(A), 4, 1, C128, P(B), 0, None) == CUDA
+    assert b"injected" in lib.pauli_last_error()
+    lib.pauli_debug_fail_next_launches(0)
