@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=14, help="qubits of the timed workload")
     p.add_argument("--quick", action="store_true", help="skip the secondary forms")
+    p.add_argument("--variant", default="default", choices=["default", "unit8192", "unit4096"],
+                   help="XOR-diagonal launch shape of the timed step")
     p.add_argument("--profile", action="store_true",
                    help="only warm-up + timed kernel launches (for ncu); prints the step time")
     return p.parse_args()
@@ -243,6 +245,9 @@ def run_ours(args):
     G = torch.from_numpy(G_h).to(dev)
     out = torch.empty(ncoef, dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    if args.variant != "default":
+        pg.set_variant(N, torch.complex128, "decompose", args.variant)
 
     def step():
         pg.decompose(G, out=out, method="xordiag")

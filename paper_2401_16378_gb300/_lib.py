@@ -35,6 +35,8 @@ SIGNATURES = {
     "pauli_plan_status": (_i, [_vp]),
     "pauli_plan_set_stall": (_i, [_vp, _i]),
     "pauli_plan_destroy": (None, [_vp]),
+    "pauli_set_variant": (_i, [_i, _i, _i, _i]),
+    "pauli_get_variant": (_i, [_i, _i, _i]),
     "pauli_last_error": (ctypes.c_char_p, []),
     "pauli_version": (_i, []),
     "pauli_debug_fail_next_launches": (None, [_i]),

@@ -177,6 +177,7 @@ class PauliPlan:
         check(self._lib.pauli_plan_graph_launch(self._h, _stream(stream)))
 
     def status(self) -> int:
+        """Synchronise and return the plan's status (0 = PAULI_OK, 8 = PAULI_ERR_TIMEOUT)."""
         return int(self._lib.pauli_plan_status(self._h))
 
     def set_stall(self, stall: bool) -> None:
@@ -209,6 +210,19 @@ class PauliDecompose(torch.autograd.Function):
 
 def decompose_autograd(G: torch.Tensor, method="auto") -> torch.Tensor:
     return PauliDecompose.apply(G, method)
+
+
+VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2}
+
+
+def set_variant(N: int, dtype: torch.dtype, op: str, variant) -> None:
+    """Select the XOR-diagonal launch shape for (N, dtype, op in {"decompose", "compose"})."""
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    check(_lib.load().pauli_set_variant(int(N), _DTYPES[dtype], {"decompose": 0, "compose": 1}[op], v))
+
+
+def get_variant(N: int, dtype: torch.dtype, op: str) -> int:
+    return int(_lib.load().pauli_get_variant(int(N), _DTYPES[dtype], {"decompose": 0, "compose": 1}[op]))
 
 
 def last_error() -> str:

@@ -7,8 +7,11 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+
 #include "kernels.h"
 #include "pauli.h"
+#include "plan_internal.h"
 
 namespace {
 
@@ -137,6 +140,22 @@ int pauli_compose(const void* c, int N, int count, int dtype, void* G_out, int s
   return PAULI_OK;
 }
 
+int pauli_set_variant(int N, int dtype, int op, int variant) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (op != 0 && op != 1) return fail(PAULI_ERR_ARG, "op = %d is not 0 (decompose) or 1 (compose)", op);
+  if (variant != PAULI_VARIANT_DEFAULT && !pauli::xordiag_variant_supported(variant, N))
+    return fail(PAULI_ERR_UNSUPPORTED, "variant %d has no kernel for N = %d", variant, N);
+  pauli::xordiag_set_variant(N, dtype == PAULI_C64, op == 1, variant);
+  return PAULI_OK;
+}
+
+int pauli_get_variant(int N, int dtype, int op) {
+  if (check_dtype(dtype) || check_n(N) || (op != 0 && op != 1)) return 0;
+  return pauli::xordiag_get_variant(N, dtype == PAULI_C64, op == 1);
+}
+
 int pauli_coeffs_at(const void* G, int N, int dtype, const uint64_t* idx, int64_t k, void* out, void* stream) {
   int st;
   if ((st = check_dtype(dtype))) return st;
@@ -198,30 +217,88 @@ int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* 
 struct pauli_plan {
   std::vector<int> Ns;
   int dtype = PAULI_C128;
-  std::vector<const void*> in;
-  std::vector<void*> out;
+  int UB = 13;
+  int blocks_per_sm = 0;
+  int n_items = 0;
+  pauli::PlanItem* d_items = nullptr;
+  pauli::PlanMat* d_mats = nullptr;
+  pauli::PlanCtrl* d_ctrl = nullptr;
   bool bound = false;
   cudaStream_t last = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t graph = nullptr;
 };
+
+namespace {
+
+void plan_free(pauli_plan* p) {
+  if (!p) return;
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->capture) cudaStreamDestroy(p->capture);
+  cudaFree(p->d_items);
+  cudaFree(p->d_mats);
+  cudaFree(p->d_ctrl);
+  delete p;
+}
+
+int plan_enqueue(pauli_plan* p, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(int), s);  // counter, status
+  if (e != cudaSuccess) return cuda_fail(e, "plan reset");
+  e = pauli::launch_plan(p->d_items, p->n_items, p->d_mats, p->d_ctrl, p->dtype == PAULI_C64, p->UB, p->blocks_per_sm,
+                         s);
+  if (e != cudaSuccess) return cuda_fail(e, "plan launch");
+  return PAULI_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
 int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
                       pauli_plan** plan) {
-  (void)threads_per_block;
-  (void)blocks_per_sm;
   int st;
   if (!plan) return fail(PAULI_ERR_NULL, "plan is NULL");
   *plan = nullptr;
   if ((st = check_dtype(dtype))) return st;
   if (batch < 1) return fail(PAULI_ERR_ARG, "batch = %d must be >= 1", batch);
   if (!N_list) return fail(PAULI_ERR_NULL, "N_list is NULL");
+  if (threads_per_block != 0 && threads_per_block != 256 && threads_per_block != 512)
+    return fail(PAULI_ERR_ARG, "threads_per_block = %d is not 0, 256 or 512", threads_per_block);
+  if (blocks_per_sm < 0) return fail(PAULI_ERR_ARG, "blocks_per_sm = %d must be >= 0", blocks_per_sm);
   for (int b = 0; b < batch; ++b)
     if (N_list[b] < 1 || N_list[b] > 10) return fail(PAULI_ERR_ARG, "N_list[%d] = %d outside [1, 10]", b, N_list[b]);
   pauli_plan* p = new (std::nothrow) pauli_plan;
   if (!p) return fail(PAULI_ERR_NOMEM, "plan allocation failed");
   p->Ns.assign(N_list, N_list + batch);
   p->dtype = dtype;
+  p->UB = threads_per_block == 256 ? 12 : 13;
+  p->blocks_per_sm = blocks_per_sm;
+  // work list: one item per unit (or per small matrix), largest N first
+  std::vector<pauli::PlanItem> items;
+  const int nmin = pauli::plan_min_unit_n(p->UB);
+  std::vector<int> order(batch);
+  for (int b = 0; b < batch; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return N_list[a] > N_list[b]; });
+  for (int b : order) {
+    const int N = N_list[b];
+    const unsigned units = N >= nmin ? (unsigned)((1ull << (2 * N)) >> p->UB) : 1u;
+    for (unsigned u = 0; u < units; ++u) items.push_back(pauli::PlanItem{(uint32_t)b, u});
+  }
+  p->n_items = (int)items.size();
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_items, items.size() * sizeof(pauli::PlanItem))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_mats, batch * sizeof(pauli::PlanMat))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_ctrl, sizeof(pauli::PlanCtrl))) != cudaSuccess) {
+    plan_free(p);
+    return fail(PAULI_ERR_NOMEM, "plan device allocation failed: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(pauli::PlanItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_ctrl, 0, sizeof(pauli::PlanCtrl));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    plan_free(p);
+    return cuda_fail(e, "pauli_plan_create");
+  }
   *plan = p;
   return PAULI_OK;
 }
@@ -229,12 +306,14 @@ int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_b
 int pauli_plan_bind(pauli_plan* p, const void* const* G_list, void* const* out_list) {
   if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
   if (!G_list || !out_list) return fail(PAULI_ERR_NULL, "G_list and out_list must not be NULL");
+  std::vector<pauli::PlanMat> mats(p->Ns.size());
   for (size_t b = 0; b < p->Ns.size(); ++b) {
     int st = check_pair(G_list[b], "G_list[b]", p->Ns[b], 1, p->dtype, out_list[b], "out_list[b]");
     if (st) return fail(st, "entry %zu: %s", b, g_err.c_str());
+    mats[b] = pauli::PlanMat{G_list[b], out_list[b], p->Ns[b], 0};
   }
-  p->in.assign(G_list, G_list + p->Ns.size());
-  p->out.assign(out_list, out_list + p->Ns.size());
+  cudaError_t e = cudaMemcpy(p->d_mats, mats.data(), mats.size() * sizeof(pauli::PlanMat), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_plan_bind");
   p->bound = true;
   return PAULI_OK;
 }
@@ -242,29 +321,58 @@ int pauli_plan_bind(pauli_plan* p, const void* const* G_list, void* const* out_l
 int pauli_plan_execute(pauli_plan* p, void* stream) {
   if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
   if (!p->bound) return fail(PAULI_ERR_ARG, "plan has no bound buffers (call pauli_plan_bind)");
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
   p->last = (cudaStream_t)stream;
-  for (size_t b = 0; b < p->Ns.size(); ++b) {
-    int st = decompose_checked(p->in[b], p->Ns[b], 1, p->dtype, p->out[b], PAULI_AUTO, p->last);
-    if (st) return st;
-  }
-  return PAULI_OK;
+  return plan_enqueue(p, p->last);
 }
 
-int pauli_plan_graph_launch(pauli_plan* p, void* stream) { return pauli_plan_execute(p, stream); }
+int pauli_plan_graph_launch(pauli_plan* p, void* stream) {
+  if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
+  if (!p->bound) return fail(PAULI_ERR_ARG, "plan has no bound buffers (call pauli_plan_bind)");
+  if (!p->graph) {
+    // capture on the plan's own stream (the caller's may be the legacy default stream)
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "plan capture");
+    int st = plan_enqueue(p, p->capture);
+    e = cudaStreamEndCapture(p->capture, &g);
+    if (st) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "plan capture end");
+    e = cudaGraphInstantiate(&p->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->graph = nullptr;
+      return cuda_fail(e, "plan graph instantiate");
+    }
+  }
+  p->last = (cudaStream_t)stream;
+  cudaError_t e = cudaGraphLaunch(p->graph, p->last);
+  if (e != cudaSuccess) return cuda_fail(e, "plan graph launch");
+  return PAULI_OK;
+}
 
 int pauli_plan_status(pauli_plan* p) {
   if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
   cudaError_t e = cudaStreamSynchronize(p->last);
   if (e != cudaSuccess) return cuda_fail(e, "pauli_plan_status");
+  int status = 0;
+  e = cudaMemcpy(&status, &p->d_ctrl->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_plan_status");
+  if (status) return fail(status, "a bounded wait in the plan kernel gave up");
   return PAULI_OK;
 }
 
 int pauli_plan_set_stall(pauli_plan* p, int stall) {
-  (void)stall;
   if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
-  return fail(PAULI_ERR_UNSUPPORTED, "stall hook not built");
+  const int v = stall ? 1 : 0;
+  cudaError_t e = cudaMemcpy(&p->d_ctrl->stall, &v, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_plan_set_stall");
+  return PAULI_OK;
 }
 
-void pauli_plan_destroy(pauli_plan* p) { delete p; }
+void pauli_plan_destroy(pauli_plan* p) { plan_free(p); }
 
 }  // extern "C"

@@ -14,8 +14,15 @@ cudaError_t launch_coeffs_at(const void* G, int N, bool c64, const uint64_t* idx
 
 // XOR-diagonal gather + Walsh-Hadamard transform (xordiag.cu). compose = the inverse map
 // scaled by 2^scale_exp. Returns cudaErrorNotSupported when N has no XOR-diagonal kernel.
+// Variants (launch shapes): 8192-element units on 512-thread CTAs, or 4096-element units on
+// 256-thread CTAs (two per SM); 0 selects the tuned or built-in choice.
+constexpr int kVariantUnit13 = 1;
+constexpr int kVariantUnit12 = 2;
 bool xordiag_supported(int N);
+bool xordiag_variant_supported(int variant, int N);
+int xordiag_get_variant(int N, bool c64, bool compose);
+void xordiag_set_variant(int N, bool c64, bool compose, int variant);
 cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, bool compose, int scale_exp, void* out,
-                           cudaStream_t s);
+                           cudaStream_t s, int variant = 0);
 
 }  // namespace pauli

@@ -1,0 +1,409 @@
+// xordiag_impl.cuh -- building blocks of the XOR-diagonal kernels (see xordiag.cu): unit
+// layouts, the shared-memory exchange, fixed-point conversions and arithmetic policies.
+#pragma once
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace pauli {
+namespace xd {
+
+// A unit holds 2^UB elements, 16 per thread: UB = 13 -> 512 threads, one CTA per SM;
+// UB = 12 -> 256 threads, two CTAs per SM (one loads while the other computes).
+template <int UB>
+struct Unit {
+  static constexpr int kThreads = 1 << (UB - 4);
+  static constexpr int kMinBlocks = UB == 12 ? 2 : 1;
+  static constexpr size_t kSmem = (size_t)16 << UB;
+};
+
+// Shared-memory slot swizzle: the low 3 bits of a 16-byte slot index are XORed with a
+// linear function of its higher bits. The columns were chosen so that in every exchange
+// of every layout below (both unit sizes, and the cluster combine) the 8 lanes of each
+// quarter-warp touch 8 distinct bank groups.
+__host__ __device__ constexpr uint32_t swz_col(int p) {
+  return p == 3 ? 7u : p == 4 ? 4u : p == 5 ? 2u : p == 6 ? 7u : p == 7 ? 0u : p == 8 ? 1u : p == 9 ? 7u
+       : p == 10 ? 3u : p == 11 ? 4u : p == 12 ? 0u : 0u;
+}
+__host__ __device__ constexpr uint32_t swz_term(uint32_t u) {
+  uint32_t f = 0;
+  for (int p = 3; p < 13; ++p)
+    if ((u >> p) & 1u) f ^= swz_col(p);
+  return f;
+}
+// 16-byte shared-memory accesses (one instruction each)
+__device__ __forceinline__ void sts128(uint32_t addr, const uint4& v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr) : "memory");
+  return v;
+}
+__host__ __device__ constexpr uint32_t spread_c(uint32_t v) {
+  uint32_t r = 0;
+  for (int b = 0; b < 16; ++b) r |= ((v >> b) & 1u) << (2 * b);
+  return r;
+}
+
+// Layout of a unit of 2^UB elements for L transformed row bits and K = UB - L class bits.
+// Element index u = class | (row << K). Phase p transforms the row bits
+// [gstart, gstart + gcount); its registers hold those bits (padded with the lowest other row
+// bits), its UB - 4 thread-index bits hold the remaining u bits in ascending order, so lanes
+// always vary the class bits first: coalesced sectors on load and store.
+template <int UB, int L>
+struct Layout {
+  static constexpr int K = UB - L;
+  static constexpr int NPH = L >= 9 ? 3 : 2;
+  __host__ __device__ static constexpr int gstart(int p) { return L >= 9 ? (p == 0 ? 8 : (p == 1 ? 0 : 4)) : (p == 0 ? 4 : 0); }
+  __host__ __device__ static constexpr int gcount(int p) { return L >= 9 ? (p == 0 ? L - 8 : 4) : (p == 0 ? L - 4 : 4); }
+  __host__ __device__ static constexpr bool in_group(int p, int b) { return b >= gstart(p) && b < gstart(p) + gcount(p); }
+  __host__ __device__ static constexpr int regpos(int p, int k) {
+    if (k < gcount(p)) return K + gstart(p) + k;
+    int need = k - gcount(p);
+    for (int b = 0; b < L; ++b)
+      if (!in_group(p, b)) {
+        if (need == 0) return K + b;
+        --need;
+      }
+    return -1;
+  }
+  __host__ __device__ static constexpr bool is_reg(int p, int pos) {
+    for (int k = 0; k < 4; ++k)
+      if (regpos(p, k) == pos) return true;
+    return false;
+  }
+  __host__ __device__ static constexpr int thrpos(int p, int k) {
+    int need = k;
+    for (int pos = 0; pos < UB; ++pos)
+      if (!is_reg(p, pos)) {
+        if (need == 0) return pos;
+        --need;
+      }
+    return -1;
+  }
+  __host__ __device__ static constexpr uint32_t reg_u(int p, int j) {
+    uint32_t u = 0;
+    for (int k = 0; k < 4; ++k)
+      if ((j >> k) & 1) u |= 1u << regpos(p, k);
+    return u;
+  }
+  __device__ static __forceinline__ uint32_t thread_u(int p, uint32_t t) {
+    uint32_t u = 0;
+#pragma unroll
+    for (int k = 0; k < UB - 4; ++k) u |= ((t >> k) & 1u) << thrpos(p, k);
+    return u;
+  }
+};
+
+// ------------------------------------------------------- fixed point <-> FP64 (integer only) --
+// 53-bit significand (mh:lo) >> r for r >= 0 (r >= 64 gives 0), mh < 2^31.
+__device__ __forceinline__ unsigned long long shr_sig(uint32_t mh, uint32_t lo, int r) {
+  const uint32_t h = mh >> min(r, 31);
+  const uint32_t l = r < 32 ? __funnelshift_r(lo, mh, r) : (mh >> min(r - 32, 31));
+  return ((unsigned long long)h << 32) | l;
+}
+
+// Per-class conversion state of the complex128 path.
+struct FixConv {
+  int rbase;   // right shift of the (pre-shifted) significand is rbase - exponent field
+  int obias;   // biased FP64 exponent of 2^63 * output scale
+  bool slow;   // tiny class maximum: zeros and underflow need the general path
+  bool nan;    // class contains Inf or NaN
+};
+
+// round-toward-zero(v * 2^s) of the double (hi, lo) as int64; LPRE = max(0, 9 - N) is a
+// constant left pre-shift so that the remaining shift is always to the right. Zero and
+// subnormal inputs give 0.
+template <int LPRE>
+__device__ __forceinline__ long long to_fixed(uint32_t hi, uint32_t lo, const FixConv& cv) {
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
+  uint32_t ml = lo;
+  if (LPRE > 0) {
+    mh = __funnelshift_l(ml, mh, LPRE);
+    ml <<= LPRE;
+  }
+  int r = cv.rbase - e;
+  if (cv.slow) r = e ? r : 127;  // zero / subnormal (only reachable when rbase < 64)
+  const long long mag = (long long)shr_sig(mh, ml, r);
+  const long long sg = (long long)((int)hi >> 31);
+  return (mag ^ sg) - sg;
+}
+
+// Double nearest toward zero to W * 2^(obias - 1086), sign flipped when neg = 1. |W| <= 2^62.
+__device__ __forceinline__ double from_fixed(long long W, const FixConv& cv, uint32_t neg) {
+  const uint32_t sg = ((uint32_t)((unsigned long long)W >> 63)) ^ neg;
+  const unsigned long long a = (unsigned long long)(W < 0 ? -W : W);
+  const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
+  uint32_t mh, ml;
+  int lz;
+  if (ah != 0u) {
+    lz = __clz(ah);
+    mh = __funnelshift_l(al, ah, lz);
+    ml = al << lz;
+  } else {  // |W| < 2^32 (tiny relative to the class) or zero
+    lz = 32 + __clz(al);
+    mh = al << (lz & 31);
+    ml = 0u;
+  }
+  const int e = cv.obias - lz;  // biased exponent of the result
+  uint32_t hi = (mh >> 11) + ((uint32_t)(e - 1) << 20);
+  uint32_t lo = __funnelshift_r(ml, mh, 11);
+  if (a == 0ull || (cv.slow && e <= 0)) {
+    hi = 0u;
+    lo = 0u;
+  }
+  hi |= sg << 31;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// ---------------------------------------------------------------------- arithmetic policies
+struct ArC128 {
+  using Raw = uint4;  // (re.lo, re.hi, im.lo, im.hi) bit patterns
+  struct Elem {
+    long long re, im;
+  };
+  using Conv = FixConv;
+  static constexpr bool kScaled = true;
+  __device__ static __forceinline__ Raw load(const void* p, unsigned long long i) {
+    return __ldg(reinterpret_cast<const uint4*>(p) + i);
+  }
+  __device__ static __forceinline__ void prefetch(const void* p, unsigned long long i) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const uint4*>(p) + i));
+  }
+  // masked exponent fields (compare as integers)
+  __device__ static __forceinline__ uint32_t exp_key(const Raw& r) { return max(r.y & 0x7FF00000u, r.w & 0x7FF00000u); }
+  __device__ static __forceinline__ uint4 raw_pack(const Raw& r) { return r; }
+  __device__ static __forceinline__ Raw raw_unpack(const uint4& q) { return q; }
+  __device__ static __forceinline__ Conv make_conv(int N, uint32_t Ekey, int out_scale_exp) {
+    // 2^N terms of magnitude < 2^(E-1022) * 2^s must stay below 2^62: s = 1084 - N - E.
+    const int E = (int)(Ekey >> 20);
+    Conv c;
+    c.nan = E == 0x7FF;
+    const int s = (E == 0 || c.nan) ? 0 : 1084 - N - E;
+    const int lpre = N < 9 ? 9 - N : 0;
+    c.rbase = 1075 - s + lpre;
+    c.obias = 1086 + out_scale_exp - s;  // 1023 + 63 + scale
+    c.slow = c.rbase < 64 || c.obias <= 64;
+    return c;
+  }
+  // Converted element times i^k (k mod 4).
+  template <int LPRE>
+  __device__ static __forceinline__ Elem convert(const Raw& r, const Conv& cv, uint32_t k) {
+    const bool swap = k & 1u;
+    uint32_t ah = swap ? r.w : r.y, al = swap ? r.z : r.x;
+    uint32_t bh = swap ? r.y : r.w, bl = swap ? r.x : r.z;
+    ah ^= ((k ^ (k >> 1)) & 1u) << 31;  // i^k: re' = (-1)^[k in {1,2}] (k odd ? im : re)
+    bh ^= ((k >> 1) & 1u) << 31;        //       im' = (-1)^[k in {2,3}] (k odd ? re : im)
+    return Elem{to_fixed<LPRE>(ah, al, cv), to_fixed<LPRE>(bh, bl, cv)};
+  }
+  __device__ static __forceinline__ void bfly(Elem& a, Elem& b) {
+    const long long r0 = a.re + b.re, r1 = a.re - b.re, i0 = a.im + b.im, i1 = a.im - b.im;
+    a.re = r0;
+    a.im = i0;
+    b.re = r1;
+    b.im = i1;
+  }
+  __device__ static __forceinline__ uint4 pack(const Elem& a) {
+    return make_uint4((uint32_t)a.re, (uint32_t)((unsigned long long)a.re >> 32), (uint32_t)a.im,
+                      (uint32_t)((unsigned long long)a.im >> 32));
+  }
+  __device__ static __forceinline__ Elem unpack(const uint4& q) {
+    return Elem{(long long)(((unsigned long long)q.y << 32) | q.x), (long long)(((unsigned long long)q.w << 32) | q.z)};
+  }
+  // Store W * 2^scale * i^k.
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    const bool swap = k & 1u;
+    const long long x = swap ? a.im : a.re, y = swap ? a.re : a.im;
+    double2 o;
+    o.x = from_fixed(x, cv, (k ^ (k >> 1)) & 1u);
+    o.y = from_fixed(y, cv, (k >> 1) & 1u);
+    if (cv.nan) o.x = o.y = f64_nan();
+    reinterpret_cast<double2*>(p)[i] = o;
+  }
+};
+
+struct C64Conv {
+  float scale;
+};
+
+struct ArC64 {
+  using Raw = float2;
+  struct Elem {
+    float rh, rl, ih, il;
+  };
+  using Conv = C64Conv;
+  static constexpr bool kScaled = false;
+  __device__ static __forceinline__ Raw load(const void* p, unsigned long long i) {
+    return __ldg(reinterpret_cast<const float2*>(p) + i);
+  }
+  __device__ static __forceinline__ void prefetch(const void* p, unsigned long long i) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const float2*>(p) + i));
+  }
+  __device__ static __forceinline__ uint32_t exp_key(const Raw&) { return 0u; }
+  __device__ static __forceinline__ uint4 raw_pack(const Raw& r) { return make_uint4(__float_as_uint(r.x), __float_as_uint(r.y), 0u, 0u); }
+  __device__ static __forceinline__ Raw raw_unpack(const uint4& q) { return make_float2(__uint_as_float(q.x), __uint_as_float(q.y)); }
+  __device__ static __forceinline__ Conv make_conv(int, uint32_t, int out_scale_exp) {
+    return Conv{__int_as_float((127 + out_scale_exp) << 23)};  // 2^scale, exact
+  }
+  template <int LPRE>
+  __device__ static __forceinline__ Elem convert(const Raw& r, const Conv&, uint32_t k) {
+    float re = r.x, im = r.y;
+    mul_i_pow(re, im, k);
+    return Elem{re, 0.f, im, 0.f};
+  }
+  __device__ static __forceinline__ void bfly(Elem& a, Elem& b) {
+    float s0, e0, s1, e1, t0, f0, t1, f1;
+    two_sum(a.rh, b.rh, s0, e0);
+    two_sum(a.rh, -b.rh, s1, e1);
+    two_sum(a.ih, b.ih, t0, f0);
+    two_sum(a.ih, -b.ih, t1, f1);
+    const float l0 = __fadd_rn(__fadd_rn(a.rl, b.rl), e0), l1 = __fadd_rn(__fsub_rn(a.rl, b.rl), e1);
+    const float m0 = __fadd_rn(__fadd_rn(a.il, b.il), f0), m1 = __fadd_rn(__fsub_rn(a.il, b.il), f1);
+    a = Elem{s0, l0, t0, m0};
+    b = Elem{s1, l1, t1, m1};
+  }
+  __device__ static __forceinline__ uint4 pack(const Elem& a) {
+    return make_uint4(__float_as_uint(a.rh), __float_as_uint(a.rl), __float_as_uint(a.ih), __float_as_uint(a.il));
+  }
+  __device__ static __forceinline__ Elem unpack(const uint4& q) {
+    return Elem{__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), __uint_as_float(q.w)};
+  }
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    float re = __fadd_rn(a.rh, a.rl), im = __fadd_rn(a.ih, a.il);
+    mul_i_pow(re, im, k);
+    reinterpret_cast<float2*>(p)[i] = make_float2(__fmul_rn(re, cv.scale), __fmul_rn(im, cv.scale));
+  }
+};
+
+// Butterflies over the low G register-index bits.
+template <class AR, int G>
+__device__ __forceinline__ void wht_regs(typename AR::Elem (&v)[16]) {
+#pragma unroll
+  for (int b = 0; b < G; ++b)
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (!((j >> b) & 1)) AR::bfly(v[j], v[j | (1 << b)]);
+}
+
+template <class LY, class AR, int P>
+__device__ __forceinline__ void exchange(typename AR::Elem (&v)[16], uint32_t xaddr, uint32_t t) {
+  __syncthreads();
+  // slot(u) = u ^ swz(u) is XOR-linear: slot(thread part) ^ slot(register part); the XOR is
+  // taken on slot indices, and the base address is added afterwards.
+  const uint32_t ut = LY::thread_u(P, t);
+  const uint32_t ft = ut ^ swz_term(ut);
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    sts128(xaddr + 16u * (ft ^ (LY::reg_u(P, j) ^ swz_term(LY::reg_u(P, j)))), AR::pack(v[j]));
+  __syncthreads();
+  const uint32_t un = LY::thread_u(P + 1, t);
+  const uint32_t fn = un ^ swz_term(un);
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    v[j] = AR::unpack(lds128(xaddr + 16u * (fn ^ (LY::reg_u(P + 1, j) ^ swz_term(LY::reg_u(P + 1, j))))));
+}
+
+// Global element index of (class x, index y = y_t | y_j) where the thread part y_t and the
+// register part y_j have disjoint bits:
+//   MATRIX: G[y, y ^ x] = y_t*D + (y_t ^ x) + y_j*D ^ y_j (per-element: one add, one xor)
+//   COEFFS: c[n(x, y)]  = n(x, y_t) ^ 3*spread(y_j)   (n(x, z): even bits x^z, odd bits z)
+template <int N, bool MATRIX>
+struct Addr {
+  unsigned long long tb;  // thread part
+  uint32_t q;             // y_t ^ x (matrix case)
+  __device__ __forceinline__ void init(unsigned long long base, uint32_t x, uint32_t yt) {
+    if (MATRIX) {
+      tb = base + (unsigned long long)yt * (1ull << N);
+      q = yt ^ x;
+    } else {
+      tb = base + pauli_index(x, yt);
+      q = 0;
+    }
+  }
+  __device__ __forceinline__ unsigned long long at(uint32_t yj) const {
+    if (MATRIX) return tb + ((unsigned long long)yj << N) + (q ^ yj);
+    return tb ^ (unsigned long long)(3u * spread_c(yj));
+  }
+};
+
+
+// ------------------------------------------------------------- one single-CTA work unit --
+// Classes [xb, xb + 2^K) of the N-qubit matrix whose elements start at index `base` of in/out
+// (decompose: in = G, out = c; compose: in = c, out = G). smax holds 2^K words. prefetch()
+// is called once the unit's own loads are in flight.
+template <int UB, int N, class AR, bool COMPOSE, class Prefetch>
+__device__ __forceinline__ void run_unit(const void* __restrict__ in, void* __restrict__ out, unsigned long long base,
+                                         uint32_t xb, int scale_exp, uint32_t xaddr, uint32_t* smax, uint32_t t,
+                                         Prefetch prefetch) {
+  using LY = Layout<UB, N>;
+  constexpr int K = LY::K;
+  constexpr int LAST = LY::NPH - 1;
+  constexpr int LPRE = N < 9 ? 9 - N : 0;
+  const uint32_t c = t & ((1u << K) - 1u);  // class bits are the lowest thread bits in every phase
+  const uint32_t x = xb | c;
+  const uint32_t y0 = LY::thread_u(0, t) >> K;  // thread part of the load-phase index
+  const uint32_t yl = LY::thread_u(LAST, t) >> K;
+  const int out_scale = COMPOSE ? scale_exp : -N;
+  Addr<N, !COMPOSE> ain;
+  ain.init(base, x, y0);
+  typename AR::Raw raw[16];
+  uint32_t emax = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    raw[j] = AR::load(in, ain.at(LY::reg_u(0, j) >> K));
+    emax = max(emax, AR::exp_key(raw[j]));
+  }
+  prefetch();
+  uint32_t Ekey = 0;
+  if constexpr (AR::kScaled) {
+    if (t < (1u << K)) smax[t] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int m = 1 << K; m < 32; m <<= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, m));
+    if (((t & 31u) >> K) == 0) atomicMax(&smax[c], emax);
+    __syncthreads();
+    Ekey = smax[c];
+  }
+  const typename AR::Conv cv = AR::make_conv(N, Ekey, out_scale);
+  typename AR::Elem v[16];
+  {
+    const uint32_t kt = COMPOSE ? 3u * (uint32_t)__popc(x & y0) : 0u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t k = COMPOSE ? kt + 3u * (uint32_t)__popc(x & (LY::reg_u(0, j) >> K)) : 0u;  // (-i)^popc(x&z)
+      v[j] = AR::template convert<LPRE>(raw[j], cv, k);
+    }
+  }
+  wht_regs<AR, LY::gcount(0)>(v);
+  exchange<LY, AR, 0>(v, xaddr, t);
+  wht_regs<AR, LY::gcount(1)>(v);
+  if constexpr (LY::NPH == 3) {
+    exchange<LY, AR, 1>(v, xaddr, t);
+    wht_regs<AR, LY::gcount(2)>(v);
+  }
+  Addr<N, COMPOSE> ao;
+  ao.init(base, x, yl);
+  const uint32_t kt = COMPOSE ? 0u : (uint32_t)__popc(x & yl);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const uint32_t yj = LY::reg_u(LAST, j) >> K;
+    const uint32_t k = COMPOSE ? 0u : kt + (uint32_t)__popc(x & yj);  // i^popc(x&z)
+    AR::store(out, ao.at(yj), v[j], cv, k);
+  }
+}
+
+// L2 prefetch of the elements run_unit will load for classes [xb, xb + 2^K).
+template <int UB, int N, class AR, bool COMPOSE>
+__device__ __forceinline__ void unit_prefetch(const void* in, unsigned long long base, uint32_t xb, uint32_t t) {
+  using LY = Layout<UB, N>;
+  constexpr int K = LY::K;
+  Addr<N, !COMPOSE> an;
+  an.init(base, xb | (t & ((1u << K) - 1u)), LY::thread_u(0, t) >> K);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) AR::prefetch(in, an.at(LY::reg_u(0, j) >> K));
+}
+
+}  // namespace xd
+}  // namespace pauli

@@ -68,6 +68,10 @@ def test_decompose_rejects_bad_arguments(lib):
     assert lib.pauli_decompose(P(A), 4, 1, C128, P(A + 16 * 255), 0, None) == ALIAS
     assert lib.pauli_decompose(P(A), 4, 1, C128, P(B), 9, None) == ARG
     assert lib.pauli_decompose(P(A), 3, 1, C128, P(B), 2, None) == UNSUP  # no XOR-diagonal kernel at N=3
+    assert lib.pauli_set_variant(5, C128, 0, 1) == UNSUP
+    assert lib.pauli_set_variant(14, C128, 2, 1) == ARG
+    assert lib.pauli_get_variant(3, C128, 0) == 0
+    assert lib.pauli_get_variant(14, C128, 0) == 1
 
 
 def test_error_message_names_the_problem(lib):

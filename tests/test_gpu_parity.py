@@ -304,3 +304,33 @@ def test_n15_kronecker_factorises():
     # the complex64 product A (x) B is rounded once; compare against the rounded input's terms
     err = np.max(np.abs(got[nA * 4 ** 8 + nB] - want))
     assert err <= 2e-6 * np.max(np.abs(A)) * np.max(np.abs(B))
+
+
+# ------------------------------------------------------------- launch-shape variants --
+@pytest.mark.parametrize("N", [6, 8, 11, 12, 13, 14])
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_variants_agree_with_oracle(N, dtype):
+    """Both XOR-diagonal launch shapes match the oracle; complex128 results are bit-identical
+    across shapes (the transform is exact integer arithmetic)."""
+    G = workloads.gaussian_complex(N, 900 + N)
+    Gd = dev(G.astype(NP[dtype]))
+    idx = workloads.sample_indices(N, 901, k=512)
+    want = oracle.decompose_at(ref_for(G, dtype), idx)
+    results = {}
+    try:
+        for v in ("unit8192", "unit4096"):
+            ok = (v == "unit8192" and 7 <= N <= 15) or (v == "unit4096" and 6 <= N <= 14)
+            if not ok:
+                continue
+            pg.set_variant(N, dtype, "decompose", v)
+            pg.set_variant(N, dtype, "compose", v)
+            c = pg.decompose(Gd, method="xordiag")
+            results[v] = host(c)
+            assert_close(results[v][idx.astype(np.int64)], want, G, dtype)
+            back = host(pg.compose(c))
+            assert np.max(np.abs(back - G.astype(NP[dtype]))) <= 4 * TOL[dtype] * maxabs(G)
+    finally:
+        pg.set_variant(N, dtype, "decompose", "default")
+        pg.set_variant(N, dtype, "compose", "default")
+    if dtype == torch.complex128 and len(results) == 2:
+        np.testing.assert_array_equal(results["unit8192"], results["unit4096"])
