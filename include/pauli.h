@@ -121,8 +121,13 @@ int pauli_plan_set_stall(pauli_plan* plan, int stall);
 void pauli_plan_destroy(pauli_plan* plan);
 
 /* ---- Launch-shape variants of PAULI_XORDIAG ----------------------------------------------
- * PAULI_VARIANT_UNIT8192: 8192-element work units on 512-thread CTAs, one per SM (N 7..15).
- * PAULI_VARIANT_UNIT4096: 4096-element work units on 256-thread CTAs, two per SM (N 6..14).
+ * PAULI_VARIANT_UNIT8192:   8192-element work units, 512-thread CTAs (16 elements per thread,
+ *                           one CTA per SM), N 7..15.
+ * PAULI_VARIANT_UNIT4096:   4096-element work units, 256-thread CTAs (16 per thread, two CTAs
+ *                           per SM), N 6..14.
+ * PAULI_VARIANT_UNIT4096X8: 4096-element work units, 512-thread CTAs (8 per thread, two CTAs
+ *                           per SM), N 6..14.
+ * PAULI_VARIANT_UNIT8192X8: 8192-element work units, 1024-thread CTAs (8 per thread), N 7..15.
  * For N above 12 (resp. 11) a unit is one pair of XY-masks spread over a CTA cluster. Both
  * compute bit-identical complex128 results (the transform is exact integer arithmetic);
  * they differ only in speed. The choice is process-wide per (N, dtype, op), op 0 =
@@ -131,6 +136,8 @@ void pauli_plan_destroy(pauli_plan* plan);
 #define PAULI_VARIANT_DEFAULT 0
 #define PAULI_VARIANT_UNIT8192 1
 #define PAULI_VARIANT_UNIT4096 2
+#define PAULI_VARIANT_UNIT4096X8 3
+#define PAULI_VARIANT_UNIT8192X8 4
 int pauli_set_variant(int N, int dtype, int op, int variant);
 /* The variant in effect for (N, dtype, op), or 0 when PAULI_XORDIAG has none for N. */
 int pauli_get_variant(int N, int dtype, int op);

@@ -212,7 +212,7 @@ def decompose_autograd(G: torch.Tensor, method="auto") -> torch.Tensor:
     return PauliDecompose.apply(G, method)
 
 
-VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2}
+VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4}
 
 
 def set_variant(N: int, dtype: torch.dtype, op: str, variant) -> None:

@@ -28,7 +28,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotu
 _DT = {"c128": torch.complex128, "c64": torch.complex64}
 _DT_CODE = {"c128": _lib.PAULI_C128, "c64": _lib.PAULI_C64}
 _OPS = {"decompose": 0, "compose": 1}
-VARIANT_RANGE = {1: (7, 15), 2: (6, 14)}  # variant -> supported N range
+VARIANT_RANGE = {1: (7, 15), 2: (6, 14), 3: (6, 14), 4: (7, 15)}  # variant -> supported N range
 
 
 def _gpu_name() -> str:

@@ -16,8 +16,10 @@ cudaError_t launch_coeffs_at(const void* G, int N, bool c64, const uint64_t* idx
 // scaled by 2^scale_exp. Returns cudaErrorNotSupported when N has no XOR-diagonal kernel.
 // Variants (launch shapes): 8192-element units on 512-thread CTAs, or 4096-element units on
 // 256-thread CTAs (two per SM); 0 selects the tuned or built-in choice.
-constexpr int kVariantUnit13 = 1;
-constexpr int kVariantUnit12 = 2;
+constexpr int kVariantUnit13 = 1;    // 8192-element units, 512 threads x 16 elements
+constexpr int kVariantUnit12 = 2;    // 4096-element units, 256 threads x 16 elements, 2 CTAs/SM
+constexpr int kVariantUnit12x8 = 3;  // 4096-element units, 512 threads x 8 elements, 2 CTAs/SM
+constexpr int kVariantUnit13x8 = 4;  // 8192-element units, 1024 threads x 8 elements
 bool xordiag_supported(int N);
 bool xordiag_variant_supported(int variant, int N);
 int xordiag_get_variant(int N, bool c64, bool compose);

@@ -1,175 +1,21 @@
-// plan.cu -- one persistent launch that decomposes a batch of matrices of uneven N.
-//
-// The plan's work list holds one item per work unit: for N at or above the unit size's
-// threshold an item is one XOR-diagonal unit of the matrix (2^UB elements, the same unit the
-// single-matrix kernel processes); a smaller matrix is one item, transformed whole in shared
-// memory. Items are ordered by decreasing N (largest work first). Every CTA of the persistent
-// grid takes items from a device counter, and fetches its next item early so that it can
-// prefetch that item's rows into L2 while computing the current one. The counter and a
-// status word live in a small control block that the plan resets before each launch.
+// plan.cu -- dispatch of the persistent batched plan kernel (see plan_kernels.cuh).
 #include "kernels.h"
 #include "plan_internal.h"
-#include "xordiag_impl.cuh"
 
 namespace pauli {
-namespace {
-using namespace xd;
 
-constexpr int kStallPolls = 1 << 17;  // ~0.1-1 s of polling before the wait gives up
-
-// Whole N-qubit matrix (N <= 6) in one CTA: elements u = class | (row << N) in shared memory,
-// per-class fixed-point scale, N butterfly stages in shared memory, phase and store.
-template <int N, class AR>
-__device__ void run_small(const void* __restrict__ in, void* __restrict__ out, uint32_t xaddr, uint32_t* smax,
-                          uint32_t t, uint32_t T) {
-  constexpr uint32_t D = 1u << N, E = D * D;
-  constexpr int LPRE = N < 9 ? 9 - N : 0;
-  if (AR::kScaled) {
-    for (uint32_t i = t; i < D; i += T) smax[i] = 0u;
-    __syncthreads();
-  }
-  for (uint32_t u = t; u < E; u += T) {
-    const uint32_t c = u & (D - 1u), r = u >> N;
-    const typename AR::Raw raw = AR::load(in, (unsigned long long)r * D + (r ^ c));
-    if (AR::kScaled) atomicMax(&smax[c], AR::exp_key(raw));
-    sts128(xaddr + 16u * u, AR::raw_pack(raw));
-  }
-  __syncthreads();
-  for (uint32_t u = t; u < E; u += T) {
-    const typename AR::Conv cv = AR::make_conv(N, AR::kScaled ? smax[u & (D - 1u)] : 0u, -N);
-    sts128(xaddr + 16u * u, AR::pack(AR::template convert<LPRE>(AR::raw_unpack(lds128(xaddr + 16u * u)), cv, 0u)));
-  }
-#pragma unroll
-  for (int b = 0; b < N; ++b) {
-    __syncthreads();
-    for (uint32_t p = t; p < E / 2; p += T) {
-      const uint32_t low = p & ((1u << (N + b)) - 1u);
-      const uint32_t u0 = ((p >> (N + b)) << (N + b + 1)) | low, u1 = u0 | (1u << (N + b));
-      typename AR::Elem a = AR::unpack(lds128(xaddr + 16u * u0)), e = AR::unpack(lds128(xaddr + 16u * u1));
-      AR::bfly(a, e);
-      sts128(xaddr + 16u * u0, AR::pack(a));
-      sts128(xaddr + 16u * u1, AR::pack(e));
-    }
-  }
-  __syncthreads();
-  for (uint32_t u = t; u < E; u += T) {
-    const uint32_t c = u & (D - 1u), z = u >> N;
-    const typename AR::Conv cv = AR::make_conv(N, AR::kScaled ? smax[c] : 0u, -N);
-    AR::store(out, pauli_index(c, z), AR::unpack(lds128(xaddr + 16u * u)), cv, (uint32_t)__popc(c & z));
-  }
-}
-
-// L2 prefetch of every input row segment of item `it` (128-byte lines).
-__device__ __forceinline__ void prefetch_item(const PlanItem& it, const PlanMat& m, int UB, size_t esz, uint32_t t,
-                                              uint32_t T) {
-  const uint32_t D = 1u << m.N;
-  const int small = m.N < plan_min_unit_n(UB);
-  const int K = small ? m.N : UB - m.N;
-  const uint32_t seg = (1u << K) * (uint32_t)esz;  // bytes of the unit's classes in one row
-  const uint32_t lines = seg > 128u ? seg / 128u : 1u;
-  const uint32_t xb = small ? 0u : it.unit << K;
-  const char* base = reinterpret_cast<const char*>(m.in);
-  for (uint32_t i = t; i < D * lines; i += T) {
-    const uint32_t r = i / lines, l = i % lines;
-    const unsigned long long col = (r ^ xb) & ~((1u << K) - 1u);
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((unsigned long long)r * D + col) * esz + 128ull * l));
-  }
-}
-
-template <int UB, class AR>
-__global__ void __launch_bounds__(Unit<UB>::kThreads, Unit<UB>::kMinBlocks)
-    plan_kernel(const PlanItem* __restrict__ items, int n_items, const PlanMat* __restrict__ mats, PlanCtrl* ctrl) {
-  extern __shared__ __align__(16) uint4 xbuf[];
-  __shared__ uint32_t smax[64];
-  __shared__ int s_next;
-  const uint32_t t = threadIdx.x, T = blockDim.x;
-  const uint32_t xaddr = (uint32_t)__cvta_generic_to_shared(xbuf);
-  constexpr size_t esz = sizeof(typename AR::Raw) == 16 ? 16 : 8;
-  if (blockIdx.x == 0 && t == 0 && *(volatile int*)&ctrl->stall) {
-    // Test hook: wait for a flag that nothing sets; give up after a bounded number of polls.
-    int i = 0;
-    for (; i < kStallPolls; ++i) {
-      if (*(volatile int*)&ctrl->never) break;
-      __nanosleep(2000);
-    }
-    if (i == kStallPolls) atomicExch(&ctrl->status, 8 /* PAULI_ERR_TIMEOUT */);
-  }
-  if (t == 0) s_next = atomicAdd(&ctrl->counter, 1);
-  __syncthreads();
-  int cur = s_next;
-  while (cur < n_items) {
-    __syncthreads();  // everyone has read s_next
-    if (t == 0) s_next = atomicAdd(&ctrl->counter, 1);
-    __syncthreads();
-    const int nxt = s_next;
-    const PlanItem it = items[cur];
-    const PlanMat m = mats[it.mat];
-    auto pf = [&]() {
-      if (nxt < n_items) {
-        const PlanItem in2 = items[nxt];
-        prefetch_item(in2, mats[in2.mat], UB, esz, t, T);
-      }
-    };
-#define PLAN_UNIT(NQ) run_unit<UB, NQ, AR, false>(m.in, m.out, 0ull, it.unit << (UB - NQ), 0, xaddr, smax, t, pf)
-#define PLAN_SMALL(NQ) \
-  do {                 \
-    pf();              \
-    run_small<NQ, AR>(m.in, m.out, xaddr, smax, t, T); \
-  } while (0)
-    switch (m.N) {
-      case 1: PLAN_SMALL(1); break;
-      case 2: PLAN_SMALL(2); break;
-      case 3: PLAN_SMALL(3); break;
-      case 4: PLAN_SMALL(4); break;
-      case 5: PLAN_SMALL(5); break;
-      case 6:
-        if constexpr (UB == 12) PLAN_UNIT(6); else PLAN_SMALL(6);
-        break;
-      case 7: PLAN_UNIT(7); break;
-      case 8: PLAN_UNIT(8); break;
-      case 9: PLAN_UNIT(9); break;
-      case 10: PLAN_UNIT(10); break;
-      default: break;
-    }
-#undef PLAN_UNIT
-#undef PLAN_SMALL
-    cur = nxt;
-  }
-}
-
-template <int UB, class AR>
-cudaError_t launch_plan_t(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, int blocks_per_sm,
-                          cudaStream_t s) {
-  auto kern = plan_kernel<UB, AR>;
-  constexpr size_t smem = Unit<UB>::kSmem;
-  static int resident = 0;
-  if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Unit<UB>::kThreads, smem);
-    if (e != cudaSuccess) return e;
-    resident = n > 0 ? n : 1;
-  }
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = blocks_per_sm > 0 && blocks_per_sm < resident ? blocks_per_sm : resident;
-  kern<<<sms * per_sm, Unit<UB>::kThreads, smem, s>>>(items, n_items, mats, ctrl);
-  return cudaGetLastError();
-}
-
-}  // namespace
-
-__host__ __device__ int plan_min_unit_n(int UB) { return UB == 12 ? 6 : 7; }
+cudaError_t plan_u12_c128(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
+cudaError_t plan_u12_c64(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
+cudaError_t plan_u13_c128(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
+cudaError_t plan_u13_c64(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
 
 cudaError_t launch_plan(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, bool c64, int UB,
                         int blocks_per_sm, cudaStream_t s) {
   if (UB == 12)
-    return c64 ? launch_plan_t<12, ArC64>(items, n_items, mats, ctrl, blocks_per_sm, s)
-               : launch_plan_t<12, ArC128>(items, n_items, mats, ctrl, blocks_per_sm, s);
-  return c64 ? launch_plan_t<13, ArC64>(items, n_items, mats, ctrl, blocks_per_sm, s)
-             : launch_plan_t<13, ArC128>(items, n_items, mats, ctrl, blocks_per_sm, s);
+    return c64 ? plan_u12_c64(items, n_items, mats, ctrl, blocks_per_sm, s)
+               : plan_u12_c128(items, n_items, mats, ctrl, blocks_per_sm, s);
+  return c64 ? plan_u13_c64(items, n_items, mats, ctrl, blocks_per_sm, s)
+             : plan_u13_c128(items, n_items, mats, ctrl, blocks_per_sm, s);
 }
 
 }  // namespace pauli

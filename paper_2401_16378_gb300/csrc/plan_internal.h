@@ -23,7 +23,7 @@ struct PlanCtrl {
 };
 
 // Smallest N processed as XOR-diagonal units (smaller matrices are one item each).
-__host__ __device__ int plan_min_unit_n(int UB);
+__host__ __device__ inline int plan_min_unit_n(int UB) { return UB == 12 ? 6 : 7; }
 cudaError_t launch_plan(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, bool c64, int UB,
                         int blocks_per_sm, cudaStream_t s);
 

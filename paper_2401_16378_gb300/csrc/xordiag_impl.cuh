@@ -8,11 +8,14 @@
 namespace pauli {
 namespace xd {
 
-// A unit holds 2^UB elements, 16 per thread: UB = 13 -> 512 threads, one CTA per SM;
-// UB = 12 -> 256 threads, two CTAs per SM (one loads while the other computes).
-template <int UB>
+// A unit holds 2^UB elements, 2^RB per thread in registers (RB = 4: 16 elements, RB = 3: 8):
+//   (UB, RB) = (13, 4): 512 threads, one CTA per SM   (12, 4): 256 threads, two per SM
+//              (12, 3): 512 threads, two CTAs per SM  (13, 3): 1024 threads, one per SM
+// Fewer elements per thread mean fewer registers and more resident warps to hide latency, at
+// the price of one more shared-memory exchange per unit.
+template <int UB, int RB>
 struct Unit {
-  static constexpr int kThreads = 1 << (UB - 4);
+  static constexpr int kThreads = 1 << (UB - RB);
   static constexpr int kMinBlocks = UB == 12 ? 2 : 1;
   static constexpr size_t kSmem = (size_t)16 << UB;
 };
@@ -22,8 +25,8 @@ struct Unit {
 // of every layout below (both unit sizes, and the cluster combine) the 8 lanes of each
 // quarter-warp touch 8 distinct bank groups.
 __host__ __device__ constexpr uint32_t swz_col(int p) {
-  return p == 3 ? 7u : p == 4 ? 4u : p == 5 ? 2u : p == 6 ? 7u : p == 7 ? 0u : p == 8 ? 1u : p == 9 ? 7u
-       : p == 10 ? 3u : p == 11 ? 4u : p == 12 ? 0u : 0u;
+  return p == 3 ? 7u : p == 4 ? 4u : p == 5 ? 7u : p == 6 ? 5u : p == 7 ? 3u : p == 8 ? 6u : p == 9 ? 3u
+       : p == 10 ? 1u : p == 11 ? 5u : p == 12 ? 5u : 0u;
 }
 __host__ __device__ constexpr uint32_t swz_term(uint32_t u) {
   uint32_t f = 0;
@@ -46,17 +49,25 @@ __host__ __device__ constexpr uint32_t spread_c(uint32_t v) {
   return r;
 }
 
-// Layout of a unit of 2^UB elements for L transformed row bits and K = UB - L class bits.
-// Element index u = class | (row << K). Phase p transforms the row bits
-// [gstart, gstart + gcount); its registers hold those bits (padded with the lowest other row
-// bits), its UB - 4 thread-index bits hold the remaining u bits in ascending order, so lanes
-// always vary the class bits first: coalesced sectors on load and store.
-template <int UB, int L>
+// Layout of a unit of 2^UB elements for L transformed row bits, K = UB - L class bits and RB
+// register bits. Element index u = class | (row << K). The L row bits are cut into groups of
+// at most RB bits: the top (possibly short) group first, then the others from bit 0 upwards,
+// so the lowest output bits are transformed before the last phase and sit in the lanes when
+// the unit is stored. Phase p transforms group p; its registers hold that group (padded with
+// the lowest other row bits), its UB - RB thread-index bits hold the remaining u bits in
+// ascending order, so lanes always vary the class bits first: coalesced sectors on load and
+// store.
+template <int UB, int L, int RB>
 struct Layout {
   static constexpr int K = UB - L;
-  static constexpr int NPH = L >= 9 ? 3 : 2;
-  __host__ __device__ static constexpr int gstart(int p) { return L >= 9 ? (p == 0 ? 8 : (p == 1 ? 0 : 4)) : (p == 0 ? 4 : 0); }
-  __host__ __device__ static constexpr int gcount(int p) { return L >= 9 ? (p == 0 ? L - 8 : 4) : (p == 0 ? L - 4 : 4); }
+  static constexpr int E = 1 << RB;  // elements per thread
+  static constexpr int TB = UB - RB;  // thread-index bits
+  static constexpr int FULL = L / RB, REM = L % RB;
+  static constexpr int NPH = FULL + (REM ? 1 : 0);
+  __host__ __device__ static constexpr int gstart(int p) {
+    return REM ? (p == 0 ? FULL * RB : (p - 1) * RB) : (p == 0 ? (FULL - 1) * RB : (p - 1) * RB);
+  }
+  __host__ __device__ static constexpr int gcount(int p) { return (REM && p == 0) ? REM : RB; }
   __host__ __device__ static constexpr bool in_group(int p, int b) { return b >= gstart(p) && b < gstart(p) + gcount(p); }
   __host__ __device__ static constexpr int regpos(int p, int k) {
     if (k < gcount(p)) return K + gstart(p) + k;
@@ -69,7 +80,7 @@ struct Layout {
     return -1;
   }
   __host__ __device__ static constexpr bool is_reg(int p, int pos) {
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < RB; ++k)
       if (regpos(p, k) == pos) return true;
     return false;
   }
@@ -84,32 +95,32 @@ struct Layout {
   }
   __host__ __device__ static constexpr uint32_t reg_u(int p, int j) {
     uint32_t u = 0;
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < RB; ++k)
       if ((j >> k) & 1) u |= 1u << regpos(p, k);
     return u;
   }
+  // register position k as a bit index of the row (or -1)
+  __host__ __device__ static constexpr int regrow(int p, int k) { return k < RB ? regpos(p, k) - K : -1; }
   __device__ static __forceinline__ uint32_t thread_u(int p, uint32_t t) {
     uint32_t u = 0;
 #pragma unroll
-    for (int k = 0; k < UB - 4; ++k) u |= ((t >> k) & 1u) << thrpos(p, k);
+    for (int k = 0; k < TB; ++k) u |= ((t >> k) & 1u) << thrpos(p, k);
     return u;
   }
 };
 
 // ------------------------------------------------------- fixed point <-> FP64 (integer only) --
-// 53-bit significand (mh:lo) >> r for r >= 0 (r >= 64 gives 0), mh < 2^31.
-__device__ __forceinline__ unsigned long long shr_sig(uint32_t mh, uint32_t lo, int r) {
-  const uint32_t h = mh >> min(r, 31);
-  const uint32_t l = r < 32 ? __funnelshift_r(lo, mh, r) : (mh >> min(r - 32, 31));
-  return ((unsigned long long)h << 32) | l;
-}
+// Measured on GB300 (lanes/clk/SM): integer add ~110-128, logic/shift/select/IMAD ~64,
+// int->float convert ~64, clz/popc ~16, FP64 ~2. The conversions below use adds where they can
+// and no clz, popc or FP64 instruction on their common path.
 
 // Per-class conversion state of the complex128 path.
 struct FixConv {
-  int rbase;   // right shift of the (pre-shifted) significand is rbase - exponent field
-  int obias;   // biased FP64 exponent of 2^63 * output scale
-  bool slow;   // tiny class maximum: zeros and underflow need the general path
-  bool nan;    // class contains Inf or NaN
+  int rbase;      // right shift of the (pre-shifted) significand is rbase - exponent field
+  int obias;      // biased FP64 exponent of 2^63 * output scale
+  uint32_t oexp;  // (obias - 1 - 63 + 31 + 127 ... ) folded constant, see from_fixed
+  bool slow;      // tiny class maximum: zeros and underflow need the general path
+  bool nan;       // class contains Inf or NaN
 };
 
 // round-toward-zero(v * 2^s) of the double (hi, lo) as int64; LPRE = max(0, 9 - N) is a
@@ -118,45 +129,56 @@ struct FixConv {
 template <int LPRE>
 __device__ __forceinline__ long long to_fixed(uint32_t hi, uint32_t lo, const FixConv& cv) {
   const int e = (int)((hi >> 20) & 0x7FFu);
-  uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
-  uint32_t ml = lo;
-  if (LPRE > 0) {
-    mh = __funnelshift_l(ml, mh, LPRE);
-    ml <<= LPRE;
-  }
+  unsigned long long m = ((unsigned long long)((hi & 0x000FFFFFu) | 0x00100000u) << 32) | lo;
+  if (LPRE > 0) m <<= LPRE;
   int r = cv.rbase - e;
-  if (cv.slow) r = e ? r : 127;  // zero / subnormal (only reachable when rbase < 64)
-  const long long mag = (long long)shr_sig(mh, ml, r);
+  if (cv.slow) r = e ? r : 63;  // zero / subnormal (only reachable when rbase < 64)
+  m >>= min(r, 63);             // significand < 2^55, so a shift by 63 gives 0
   const long long sg = (long long)((int)hi >> 31);
-  return (mag ^ sg) - sg;
+  return ((long long)m ^ sg) - sg;
 }
 
 // Double nearest toward zero to W * 2^(obias - 1086), sign flipped when neg = 1. |W| <= 2^62.
-__device__ __forceinline__ double from_fixed(long long W, const FixConv& cv, uint32_t neg) {
-  const uint32_t sg = ((uint32_t)((unsigned long long)W >> 63)) ^ neg;
-  const unsigned long long a = (unsigned long long)(W < 0 ? -W : W);
-  const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
-  uint32_t mh, ml;
-  int lz;
-  if (ah != 0u) {
-    lz = __clz(ah);
-    mh = __funnelshift_l(al, ah, lz);
-    ml = al << lz;
-  } else {  // |W| < 2^32 (tiny relative to the class) or zero
-    lz = 32 + __clz(al);
-    mh = al << (lz & 31);
-    ml = 0u;
-  }
-  const int e = cv.obias - lz;  // biased exponent of the result
-  uint32_t hi = (mh >> 11) + ((uint32_t)(e - 1) << 20);
-  uint32_t lo = __funnelshift_r(ml, mh, 11);
-  if (a == 0ull || (cv.slow && e <= 0)) {
-    hi = 0u;
-    lo = 0u;
-  }
-  hi |= sg << 31;
-  return __hiloint2double((int)hi, (int)lo);
+static __device__ __noinline__ double from_fixed_small(unsigned long long a, uint32_t sign, const FixConv& cv) {
+  if (a == 0ull) return __hiloint2double((int)(sign << 31), 0);
+  const int lz = __clzll((long long)a);
+  const unsigned long long m = a << lz;  // leading one at bit 63
+  const int e = cv.obias - lz;
+  if (e <= 0) return __hiloint2double((int)(sign << 31), 0);  // below the normal range
+  const uint32_t hi = (uint32_t)(m >> 43) + ((uint32_t)(e - 1) << 20);
+  return __hiloint2double((int)(hi | (sign << 31)), (int)(uint32_t)(m >> 11));
 }
+__device__ __forceinline__ double from_fixed(long long W, const FixConv& cv, uint32_t neg) {
+  const long long S = W >> 63;
+  const unsigned long long a = (unsigned long long)((W ^ S) - S);
+  const uint32_t sign = ((uint32_t)S & 1u) ^ neg;
+  const uint32_t ah = (uint32_t)(a >> 32);
+  if (ah == 0u || cv.slow) return from_fixed_small(a, sign, cv);
+  // floor(log2(ah)) from the exponent of an exact-toward-zero float conversion
+  const uint32_t fe = __float_as_uint(__uint2float_rz(ah)) >> 23;  // 127 + floor(log2 ah)
+  const uint32_t lz = 158u - fe;                                    // leading zeros of a (1..31)
+  const unsigned long long m = a << lz;                             // leading one at bit 63
+  // exponent field = obias - lz = obias - 158 + fe; the implicit one at bit 20 adds 1
+  const uint32_t hi = (uint32_t)(m >> 43) + (fe << 20) + cv.oexp;
+  return __hiloint2double((int)(hi | (sign << 31)), (int)(uint32_t)(m >> 11));
+}
+
+// popc(x & y) for a compile-time y with few bits: x's bits at those positions, pre-extracted
+// into xb[] by the caller (xb[k] = bit pos_k of x), summed with integer adds instead of popc.
+template <int P0, int P1, int P2, int P3>
+struct BitSum {
+  uint32_t b[4];
+  __device__ __forceinline__ void init(uint32_t x) {
+    b[0] = P0 >= 0 ? (x >> (P0 < 0 ? 0 : P0)) & 1u : 0u;
+    b[1] = P1 >= 0 ? (x >> (P1 < 0 ? 0 : P1)) & 1u : 0u;
+    b[2] = P2 >= 0 ? (x >> (P2 < 0 ? 0 : P2)) & 1u : 0u;
+    b[3] = P3 >= 0 ? (x >> (P3 < 0 ? 0 : P3)) & 1u : 0u;
+  }
+  // sum over the set bits k of the 4-bit index j of b[k]
+  __device__ __forceinline__ uint32_t at(int j) const {
+    return ((j & 1) ? b[0] : 0u) + ((j & 2) ? b[1] : 0u) + ((j & 4) ? b[2] : 0u) + ((j & 8) ? b[3] : 0u);
+  }
+};
 
 // ---------------------------------------------------------------------- arithmetic policies
 struct ArC128 {
@@ -185,6 +207,7 @@ struct ArC128 {
     const int lpre = N < 9 ? 9 - N : 0;
     c.rbase = 1075 - s + lpre;
     c.obias = 1086 + out_scale_exp - s;  // 1023 + 63 + scale
+    c.oexp = (uint32_t)(c.obias - 158 - 1) << 20;
     c.slow = c.rbase < 64 || c.obias <= 64;
     return c;
   }
@@ -278,31 +301,42 @@ struct ArC64 {
 };
 
 // Butterflies over the low G register-index bits.
-template <class AR, int G>
-__device__ __forceinline__ void wht_regs(typename AR::Elem (&v)[16]) {
+template <class AR, int G, int E>
+__device__ __forceinline__ void wht_regs(typename AR::Elem (&v)[E]) {
 #pragma unroll
   for (int b = 0; b < G; ++b)
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
+    for (int j = 0; j < E; ++j)
       if (!((j >> b) & 1)) AR::bfly(v[j], v[j | (1 << b)]);
 }
 
+// Re-distribute the unit between threads from phase P's layout to phase P+1's, through shared
+// memory: 16-byte slots, slot(u) = u ^ swz(u) (XOR-linear, so thread part and register part
+// combine with one XOR; the base address is added afterwards).
 template <class LY, class AR, int P>
-__device__ __forceinline__ void exchange(typename AR::Elem (&v)[16], uint32_t xaddr, uint32_t t) {
+__device__ __forceinline__ void exchange(typename AR::Elem (&v)[LY::E], uint32_t xaddr, uint32_t t) {
   __syncthreads();
-  // slot(u) = u ^ swz(u) is XOR-linear: slot(thread part) ^ slot(register part); the XOR is
-  // taken on slot indices, and the base address is added afterwards.
   const uint32_t ut = LY::thread_u(P, t);
   const uint32_t ft = ut ^ swz_term(ut);
 #pragma unroll
-  for (int j = 0; j < 16; ++j)
+  for (int j = 0; j < LY::E; ++j)
     sts128(xaddr + 16u * (ft ^ (LY::reg_u(P, j) ^ swz_term(LY::reg_u(P, j)))), AR::pack(v[j]));
   __syncthreads();
   const uint32_t un = LY::thread_u(P + 1, t);
   const uint32_t fn = un ^ swz_term(un);
 #pragma unroll
-  for (int j = 0; j < 16; ++j)
+  for (int j = 0; j < LY::E; ++j)
     v[j] = AR::unpack(lds128(xaddr + 16u * (fn ^ (LY::reg_u(P + 1, j) ^ swz_term(LY::reg_u(P + 1, j))))));
+}
+
+// All phases of the local transform: butterflies, exchange, butterflies, ...
+template <class LY, class AR, int P = 0>
+__device__ __forceinline__ void local_wht(typename AR::Elem (&v)[LY::E], uint32_t xaddr, uint32_t t) {
+  wht_regs<AR, LY::gcount(P), LY::E>(v);
+  if constexpr (P + 1 < LY::NPH) {
+    exchange<LY, AR, P>(v, xaddr, t);
+    local_wht<LY, AR, P + 1>(v, xaddr, t);
+  }
 }
 
 // Global element index of (class x, index y = y_t | y_j) where the thread part y_t and the
@@ -333,12 +367,13 @@ struct Addr {
 // Classes [xb, xb + 2^K) of the N-qubit matrix whose elements start at index `base` of in/out
 // (decompose: in = G, out = c; compose: in = c, out = G). smax holds 2^K words. prefetch()
 // is called once the unit's own loads are in flight.
-template <int UB, int N, class AR, bool COMPOSE, class Prefetch>
+template <int UB, int RB, int N, class AR, bool COMPOSE, class Prefetch>
 __device__ __forceinline__ void run_unit(const void* __restrict__ in, void* __restrict__ out, unsigned long long base,
                                          uint32_t xb, int scale_exp, uint32_t xaddr, uint32_t* smax, uint32_t t,
                                          Prefetch prefetch) {
-  using LY = Layout<UB, N>;
+  using LY = Layout<UB, N, RB>;
   constexpr int K = LY::K;
+  constexpr int E = LY::E;
   constexpr int LAST = LY::NPH - 1;
   constexpr int LPRE = N < 9 ? 9 - N : 0;
   const uint32_t c = t & ((1u << K) - 1u);  // class bits are the lowest thread bits in every phase
@@ -348,10 +383,10 @@ __device__ __forceinline__ void run_unit(const void* __restrict__ in, void* __re
   const int out_scale = COMPOSE ? scale_exp : -N;
   Addr<N, !COMPOSE> ain;
   ain.init(base, x, y0);
-  typename AR::Raw raw[16];
+  typename AR::Raw raw[E];
   uint32_t emax = 0;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < E; ++j) {
     raw[j] = AR::load(in, ain.at(LY::reg_u(0, j) >> K));
     emax = max(emax, AR::exp_key(raw[j]));
   }
@@ -367,42 +402,36 @@ __device__ __forceinline__ void run_unit(const void* __restrict__ in, void* __re
     Ekey = smax[c];
   }
   const typename AR::Conv cv = AR::make_conv(N, Ekey, out_scale);
-  typename AR::Elem v[16];
+  typename AR::Elem v[E];
   {
-    const uint32_t kt = COMPOSE ? 3u * (uint32_t)__popc(x & y0) : 0u;
+    // compose: times (-i)^popc(x&z) = i^(3 popc(x&z)), z = y0 | (register part)
+    BitSum<LY::regrow(0, 0), LY::regrow(0, 1), LY::regrow(0, 2), LY::regrow(0, 3)> xb;
+    xb.init(x);
+    const uint32_t kt = COMPOSE ? (uint32_t)__popc(x & y0) : 0u;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const uint32_t k = COMPOSE ? kt + 3u * (uint32_t)__popc(x & (LY::reg_u(0, j) >> K)) : 0u;  // (-i)^popc(x&z)
-      v[j] = AR::template convert<LPRE>(raw[j], cv, k);
-    }
+    for (int j = 0; j < E; ++j) v[j] = AR::template convert<LPRE>(raw[j], cv, COMPOSE ? 3u * (kt + xb.at(j)) : 0u);
   }
-  wht_regs<AR, LY::gcount(0)>(v);
-  exchange<LY, AR, 0>(v, xaddr, t);
-  wht_regs<AR, LY::gcount(1)>(v);
-  if constexpr (LY::NPH == 3) {
-    exchange<LY, AR, 1>(v, xaddr, t);
-    wht_regs<AR, LY::gcount(2)>(v);
-  }
+  local_wht<LY, AR>(v, xaddr, t);
   Addr<N, COMPOSE> ao;
   ao.init(base, x, yl);
-  const uint32_t kt = COMPOSE ? 0u : (uint32_t)__popc(x & yl);
+  // decompose: times i^popc(x&z), z = yl | (register part)
+  BitSum<LY::regrow(LAST, 0), LY::regrow(LAST, 1), LY::regrow(LAST, 2), LY::regrow(LAST, 3)> xo;
+  xo.init(x);
+  const uint32_t ko = COMPOSE ? 0u : (uint32_t)__popc(x & yl);
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const uint32_t yj = LY::reg_u(LAST, j) >> K;
-    const uint32_t k = COMPOSE ? 0u : kt + (uint32_t)__popc(x & yj);  // i^popc(x&z)
-    AR::store(out, ao.at(yj), v[j], cv, k);
-  }
+  for (int j = 0; j < E; ++j)
+    AR::store(out, ao.at(LY::reg_u(LAST, j) >> K), v[j], cv, COMPOSE ? 0u : ko + xo.at(j));
 }
 
 // L2 prefetch of the elements run_unit will load for classes [xb, xb + 2^K).
-template <int UB, int N, class AR, bool COMPOSE>
+template <int UB, int RB, int N, class AR, bool COMPOSE>
 __device__ __forceinline__ void unit_prefetch(const void* in, unsigned long long base, uint32_t xb, uint32_t t) {
-  using LY = Layout<UB, N>;
+  using LY = Layout<UB, N, RB>;
   constexpr int K = LY::K;
   Addr<N, !COMPOSE> an;
   an.init(base, xb | (t & ((1u << K) - 1u)), LY::thread_u(0, t) >> K);
 #pragma unroll
-  for (int j = 0; j < 16; ++j) AR::prefetch(in, an.at(LY::reg_u(0, j) >> K));
+  for (int j = 0; j < LY::E; ++j) AR::prefetch(in, an.at(LY::reg_u(0, j) >> K));
 }
 
 }  // namespace xd

@@ -318,8 +318,8 @@ def test_variants_agree_with_oracle(N, dtype):
     want = oracle.decompose_at(ref_for(G, dtype), idx)
     results = {}
     try:
-        for v in ("unit8192", "unit4096"):
-            ok = (v == "unit8192" and 7 <= N <= 15) or (v == "unit4096" and 6 <= N <= 14)
+        for v in ("unit8192", "unit4096", "unit4096x8", "unit8192x8"):
+            ok = (v.startswith("unit8192") and 7 <= N <= 15) or (v.startswith("unit4096") and 6 <= N <= 14)
             if not ok:
                 continue
             pg.set_variant(N, dtype, "decompose", v)
@@ -332,5 +332,7 @@ def test_variants_agree_with_oracle(N, dtype):
     finally:
         pg.set_variant(N, dtype, "decompose", "default")
         pg.set_variant(N, dtype, "compose", "default")
-    if dtype == torch.complex128 and len(results) == 2:
-        np.testing.assert_array_equal(results["unit8192"], results["unit4096"])
+    if dtype == torch.complex128 and len(results) > 1:
+        first = next(iter(results.values()))
+        for r in results.values():
+            np.testing.assert_array_equal(r, first)
