@@ -188,8 +188,14 @@ struct ArC128 {
   };
   using Conv = FixConv;
   static constexpr bool kScaled = true;
+  // gathered rows are touched once: no L1 allocation (it would evict useful lines), and a
+  // 128-byte L2 fetch so the neighbouring masks' sectors arrive with this one
   __device__ static __forceinline__ Raw load(const void* p, unsigned long long i) {
-    return __ldg(reinterpret_cast<const uint4*>(p) + i);
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::128B.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(reinterpret_cast<const uint4*>(p) + i));
+    return v;
   }
   __device__ static __forceinline__ void prefetch(const void* p, unsigned long long i) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const uint4*>(p) + i));
@@ -259,7 +265,11 @@ struct ArC64 {
   using Conv = C64Conv;
   static constexpr bool kScaled = false;
   __device__ static __forceinline__ Raw load(const void* p, unsigned long long i) {
-    return __ldg(reinterpret_cast<const float2*>(p) + i);
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::128B.v2.f32 {%0,%1}, [%2];"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(reinterpret_cast<const float2*>(p) + i));
+    return v;
   }
   __device__ static __forceinline__ void prefetch(const void* p, unsigned long long i) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const float2*>(p) + i));
