@@ -96,6 +96,21 @@ int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch
 int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* out_host, void* G_dev,
                          void* out_dev, int method, void* stream);
 
+/* Batched decomposition for callers that cannot allocate device memory (a fixed memory
+ * budget, an allocator that must not be re-entered, ...). Same result and same one-launch
+ * schedule as a plan over N_list, but the library allocates nothing: the work counter,
+ * status word and matrix table live in a fixed array in device global memory that is part of
+ * the library image (24,608 bytes on every GPU that loads the library, kept until the process
+ * exits). There is no counterpart in the paper; this is an interface convenience.
+ *   G_list / out_list: host arrays of `batch` device pointers; N_list: host array, values in
+ *   [1, 10]; 1 <= batch <= 1024 (larger batches are rejected with PAULI_ERR_ARG).
+ * All calls share the array: each call resets the counter and status before its launch, and
+ * calls whose kernels overlap on the GPU race on it -- serialise them (one stream, or events).
+ * The first call on a device looks up the array's device address; make it before any stream
+ * capture. Asynchronous like the other entry points. */
+int pauli_decompose_batch_static(const void* const* G_list, const int* N_list, int batch, int dtype,
+                                 void* const* out_list, void* stream);
+
 /* ---- Plans: one persistent launch over a batch of matrices of uneven N -------------------
  * A plan fixes the list of N and the dtype, owns a device work list (the matrices' x-class
  * work units ordered by descending cost), a device work counter and a device status word,

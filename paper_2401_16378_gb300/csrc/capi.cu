@@ -13,6 +13,12 @@
 #include "pauli.h"
 #include "plan_internal.h"
 
+namespace pauli {
+int static_batch_max();
+int static_batch_launch(const void* const* G_list, const int* N_list, int batch, bool c64, void* const* out_list,
+                        cudaStream_t s, const char** what, cudaError_t* cuda_err);
+}  // namespace pauli
+
 namespace {
 
 thread_local std::string g_err;
@@ -194,6 +200,29 @@ int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch
   return PAULI_OK;
 }
 
+int pauli_decompose_batch_static(const void* const* G_list, const int* N_list, int batch, int dtype,
+                                 void* const* out_list, void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if (batch < 1 || batch > pauli::static_batch_max())
+    return fail(PAULI_ERR_ARG, "batch = %d outside [1, %d] (the static scratch holds at most %d matrices)", batch,
+                pauli::static_batch_max(), pauli::static_batch_max());
+  if (!G_list || !N_list || !out_list) return fail(PAULI_ERR_NULL, "G_list, N_list and out_list must not be NULL");
+  for (int b = 0; b < batch; ++b) {
+    if (N_list[b] < 1 || N_list[b] > 10) return fail(PAULI_ERR_ARG, "N_list[%d] = %d outside [1, 10]", b, N_list[b]);
+    st = check_pair(G_list[b], "G_list[b]", N_list[b], 1, dtype, out_list[b], "out_list[b]");
+    if (st) return fail(st, "entry %d: %s", b, g_err.c_str());
+  }
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  const char* what = "";
+  cudaError_t ce = cudaSuccess;
+  st = pauli::static_batch_launch(G_list, N_list, batch, dtype == PAULI_C64, out_list, (cudaStream_t)stream, &what,
+                                  &ce);
+  if (st == PAULI_ERR_CUDA) return cuda_fail(ce, what);
+  if (st) return fail(st, "%s", what);
+  return PAULI_OK;
+}
+
 int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* out_host, void* G_dev, void* out_dev,
                          int method, void* stream) {
   int st = check_pair(G_dev, "G_dev", N, count, dtype, out_dev, "out_dev");
@@ -310,7 +339,7 @@ int pauli_plan_bind(pauli_plan* p, const void* const* G_list, void* const* out_l
   for (size_t b = 0; b < p->Ns.size(); ++b) {
     int st = check_pair(G_list[b], "G_list[b]", p->Ns[b], 1, p->dtype, out_list[b], "out_list[b]");
     if (st) return fail(st, "entry %zu: %s", b, g_err.c_str());
-    mats[b] = pauli::PlanMat{G_list[b], out_list[b], p->Ns[b], 0};
+    mats[b] = pauli::PlanMat{G_list[b], out_list[b], p->Ns[b], 0};  // items list in use: first unused
   }
   cudaError_t e = cudaMemcpy(p->d_mats, mats.data(), mats.size() * sizeof(pauli::PlanMat), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "pauli_plan_bind");

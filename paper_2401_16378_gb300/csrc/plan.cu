@@ -4,18 +4,18 @@
 
 namespace pauli {
 
-cudaError_t plan_u12_c128(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
-cudaError_t plan_u12_c64(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
-cudaError_t plan_u13_c128(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
-cudaError_t plan_u13_c64(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t);
+cudaError_t plan_u12_c128(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t, int);
+cudaError_t plan_u12_c64(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t, int);
+cudaError_t plan_u13_c128(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t, int);
+cudaError_t plan_u13_c64(const PlanItem*, int, const PlanMat*, PlanCtrl*, int, cudaStream_t, int);
 
 cudaError_t launch_plan(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, bool c64, int UB,
-                        int blocks_per_sm, cudaStream_t s) {
+                        int blocks_per_sm, cudaStream_t s, int batch) {
   if (UB == 12)
-    return c64 ? plan_u12_c64(items, n_items, mats, ctrl, blocks_per_sm, s)
-               : plan_u12_c128(items, n_items, mats, ctrl, blocks_per_sm, s);
-  return c64 ? plan_u13_c64(items, n_items, mats, ctrl, blocks_per_sm, s)
-             : plan_u13_c128(items, n_items, mats, ctrl, blocks_per_sm, s);
+    return c64 ? plan_u12_c64(items, n_items, mats, ctrl, blocks_per_sm, s, batch)
+               : plan_u12_c128(items, n_items, mats, ctrl, blocks_per_sm, s, batch);
+  return c64 ? plan_u13_c64(items, n_items, mats, ctrl, blocks_per_sm, s, batch)
+             : plan_u13_c128(items, n_items, mats, ctrl, blocks_per_sm, s, batch);
 }
 
 }  // namespace pauli

@@ -9,7 +9,7 @@ struct PlanMat {
   const void* in;
   void* out;
   int N;
-  int pad;
+  int first;  // index of this matrix's first work item (used when there is no item list)
 };
 struct PlanItem {
   uint32_t mat;   // index into the matrix table
@@ -24,7 +24,8 @@ struct PlanCtrl {
 
 // Smallest N processed as XOR-diagonal units (smaller matrices are one item each).
 __host__ __device__ inline int plan_min_unit_n(int UB) { return UB == 12 ? 6 : 7; }
+// items == nullptr: the work list is given by mats[b].first over `batch` matrices.
 cudaError_t launch_plan(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, bool c64, int UB,
-                        int blocks_per_sm, cudaStream_t s);
+                        int blocks_per_sm, cudaStream_t s, int batch = 0);
 
 }  // namespace pauli

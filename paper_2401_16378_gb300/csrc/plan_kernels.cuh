@@ -77,9 +77,24 @@ __device__ __forceinline__ void prefetch_item(const PlanItem& it, const PlanMat&
   }
 }
 
+// Item `cur` of a work list given only by the matrix table: mats[b].first is the index of
+// matrix b's first item (table ordered as the work list), found by binary search.
+__device__ __forceinline__ PlanItem item_from_table(int cur, const PlanMat* __restrict__ mats, int batch) {
+  int lo = 0, hi = batch - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (mats[mid].first <= cur)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return PlanItem{(uint32_t)lo, (uint32_t)(cur - mats[lo].first)};
+}
+
 template <int UB, class AR>
 __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlocks))
-    plan_kernel(const PlanItem* __restrict__ items, int n_items, const PlanMat* __restrict__ mats, PlanCtrl* ctrl) {
+    plan_kernel(const PlanItem* __restrict__ items, int n_items, const PlanMat* __restrict__ mats, PlanCtrl* ctrl,
+                int batch) {
   extern __shared__ __align__(16) uint4 xbuf[];
   __shared__ uint32_t smax[64];
   __shared__ int s_next;
@@ -103,11 +118,11 @@ __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlo
     if (t == 0) s_next = atomicAdd(&ctrl->counter, 1);
     __syncthreads();
     const int nxt = s_next;
-    const PlanItem it = items[cur];
+    const PlanItem it = items ? items[cur] : item_from_table(cur, mats, batch);
     const PlanMat m = mats[it.mat];
     auto pf = [&]() {
       if (nxt < n_items) {
-        const PlanItem in2 = items[nxt];
+        const PlanItem in2 = items ? items[nxt] : item_from_table(nxt, mats, batch);
         prefetch_item(in2, mats[in2.mat], UB, esz, t, T);
       }
     };
@@ -140,7 +155,7 @@ __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlo
 
 template <int UB, class AR>
 cudaError_t launch_plan_t(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, int blocks_per_sm,
-                          cudaStream_t s) {
+                          cudaStream_t s, int batch = 0) {
   auto kern = plan_kernel<UB, AR>;
   constexpr size_t smem = Unit<UB, 4>::kSmem;
   static int resident = 0;
@@ -156,7 +171,7 @@ cudaError_t launch_plan_t(const PlanItem* items, int n_items, const PlanMat* mat
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < resident ? blocks_per_sm : resident;
-  kern<<<sms * per_sm, Unit<UB, 4>::kThreads, smem, s>>>(items, n_items, mats, ctrl);
+  kern<<<sms * per_sm, Unit<UB, 4>::kThreads, smem, s>>>(items, n_items, mats, ctrl, batch);
   return cudaGetLastError();
 }
 

@@ -4,8 +4,8 @@
 namespace pauli {
 
 cudaError_t plan_u13_c64(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, int blocks_per_sm,
-                  cudaStream_t s) {
-  return pk::launch_plan_t<13, xd::ArC64>(items, n_items, mats, ctrl, blocks_per_sm, s);
+                  cudaStream_t s, int batch) {
+  return pk::launch_plan_t<13, xd::ArC64>(items, n_items, mats, ctrl, blocks_per_sm, s, batch);
 }
 
 }  // namespace pauli
