@@ -67,7 +67,7 @@ def measured_peak_hbm():
 
 def source_hash():
     h = hashlib.sha256()
-    for name in ("xordiag.cu", "common.cuh"):
+    for name in ("xordiag.cu", "xordiag_impl.cuh", "xordiag_kernels.cuh", "xordiag_c128_decompose.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2401_16378_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
