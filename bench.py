@@ -337,13 +337,13 @@ def run_ours(args):
                     "h2d_bytes_per_step": ncoef * es, "d2h_bytes_per_step": ncoef * es},
             "gpu_launches": args.steps, "clocks": clocks, "accuracy": res}
     if not args.quick:
-        line["forms"] = secondary_forms(pg, workloads, dev, stream)
+        line["forms"] = secondary_forms(pg, workloads, dev, stream, G_h)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def secondary_forms(pg, workloads, dev, stream):
+def secondary_forms(pg, workloads, dev, stream, G14=None):
     """Plain, complex64, batched and adjoint forms on the same GPU, with their errors."""
     import torch
 
@@ -383,6 +383,85 @@ def secondary_forms(pg, workloads, dev, stream):
                 entry["hbm_gbs_algorithmic"] = 2 * 4 ** N * 16 / (ms * 1e-3) / 1e9
             forms[f"n12_{name}_{method}_c128"] = entry
         del g, o
+
+    # N=14 complex64 (TwoSum-compensated FP32): time and error against the FP64 oracle
+    if G14 is not None:
+        N = 14
+        G64 = G14.astype(np.complex64)
+        g = torch.from_numpy(G64).to(dev)
+        o = torch.empty(4 ** N, dtype=torch.complex64, device=dev)
+        ms = timed(lambda: pg.decompose(g, out=o, method="xordiag"), 10)
+        idx = workloads.sample_indices(N, workloads.SEEDS["n14_idx"])
+        want = oracle.decompose_at(G64.astype(np.complex128), idx)
+        got = o.cpu().numpy()[idx.astype(np.int64)].astype(np.complex128)
+        forms["n14_xordiag_c64"] = {"ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3),
+                                    "hbm_gbs_algorithmic": 2 * 4 ** N * 8 / (ms * 1e-3) / 1e9,
+                                    "max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(G64))),
+                                    "tolerance_rel": 2e-6}
+        del g, o, G64
+
+    # batched: 512 Hermitian matrices, N uniform in 3..10, one persistent graph-captured launch
+    # against 512 separate plain launches
+    mats, Ns = workloads.batched_hermitian(workloads.SEEDS["batched"], batch=512)
+    Ns = [int(n) for n in Ns]
+    ncoef = sum(4 ** n for n in Ns)
+    rng = np.random.default_rng(5120)
+    sel = [rng.integers(0, 4 ** n, 8) for n in Ns]
+    for dname, tdt, npdt in (("c128", torch.complex128, np.complex128), ("c64", torch.complex64, np.complex64)):
+        Gd = [torch.from_numpy(G.astype(npdt)).to(dev) for G in mats]
+        outs = [torch.empty(4 ** n, dtype=tdt, device=dev) for n in Ns]
+        plan = pg.PauliPlan(Ns, dtype=tdt)
+        plan.bind(Gd, outs)
+        ms_plan = timed(plan.graph_launch, 20)
+        status = plan.status()
+        errs = []
+        for G, o, sl in zip(mats, outs, sel):
+            Gr = G.astype(npdt).astype(np.complex128)
+            got = o.cpu().numpy()[sl].astype(np.complex128)
+            errs.append(np.max(np.abs(got - oracle.decompose_at(Gr, sl.astype(np.uint64)))) / np.max(np.abs(Gr)))
+        plan.close()
+
+        def separate():
+            for g, o in zip(Gd, outs):
+                pg.decompose(g, out=o, method="plain")
+
+        ms_sep = timed(separate, 1)
+        forms[f"batched512_hermitian_{dname}"] = {
+            "plan_graph_ms": ms_plan, "plan_coeffs_per_s": ncoef / (ms_plan * 1e-3), "plan_status": status,
+            "separate_plain_ms": ms_sep, "separate_plain_coeffs_per_s": ncoef / (ms_sep * 1e-3),
+            "speedup_vs_plain": ms_sep / ms_plan, "max_err_rel": float(max(errs)),
+            "sample": "8 seeded coefficients per matrix vs the oracle"}
+        del Gd, outs
+
+    # adjoint: 64 matrices at N=10, loss = sum_n w_n |c_n|^2, forward + backward
+    N, B = 10, 64
+    A = workloads.adjoint_inputs(workloads.SEEDS["adjoint"], batch=B, N=N)
+    w = torch.from_numpy(workloads.adjoint_weights(workloads.SEEDS["adjoint_w"], N)).to(dev)
+    Gt = torch.from_numpy(A).to(dev).requires_grad_(True)
+
+    def fwd_bwd(method):
+        Gt.grad = None
+        c = pg.decompose_autograd(Gt, method=method)
+        loss = (w * c.abs() ** 2).sum()
+        loss.backward()
+        return c
+
+    ms_x = timed(lambda: fwd_bwd("xordiag"), 10)
+    c = fwd_bwd("xordiag").detach()
+    torch.cuda.synchronize(dev)
+    D = 1 << N
+    rows = np.arange(0, D, 7)
+    cols = (rows * 5 + 3) % D
+    c0 = c[0].cpu().numpy()
+    want = oracle.compose_at(2 * w.cpu().numpy() * c0, rows, cols) * 2.0 ** -N
+    got = Gt.grad[0].cpu().numpy()[rows, cols]
+    ms_p = timed(lambda: fwd_bwd("plain"), 1)
+    forms["adjoint64_n10_c128"] = {
+        "fwd_bwd_ms": ms_x, "matrices_per_s": B / (ms_x * 1e-3), "coeffs_per_s": B * 4 ** N / (ms_x * 1e-3),
+        "plain_forward_fwd_bwd_ms": ms_p, "speedup_vs_plain": ms_p / ms_x,
+        "grad_max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(want))),
+        "sample": "gradient of matrix 0 at 147 entries vs the oracle's compose of 2 w c"}
+    del Gt, A
     return forms
 
 

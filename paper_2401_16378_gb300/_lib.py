@@ -38,6 +38,7 @@ SIGNATURES = {
     "pauli_plan_destroy": (None, [_vp]),
     "pauli_set_variant": (_i, [_i, _i, _i, _i]),
     "pauli_get_variant": (_i, [_i, _i, _i]),
+    "pauli_stream_status": (_i, [_vp]),
     "pauli_last_error": (ctypes.c_char_p, []),
     "pauli_version": (_i, []),
     "pauli_debug_fail_next_launches": (None, [_i]),
@@ -69,6 +70,13 @@ def load() -> ctypes.CDLL:
                 f.restype = res
                 f.argtypes = args
             _lib = lib
+            fresh = True
+        else:
+            fresh = False
+    if fresh and os.environ.get("PAULI_AUTOTUNE", "1") != "0":
+        from . import autotune  # applies the tuned launch shapes measured on this GPU model
+
+        autotune.apply_cached()
     return _lib
 
 

@@ -212,7 +212,8 @@ def decompose_autograd(G: torch.Tensor, method="auto") -> torch.Tensor:
     return PauliDecompose.apply(G, method)
 
 
-VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4}
+VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4, "tiled8192": 5,
+            "tiled4096": 6}
 
 
 def set_variant(N: int, dtype: torch.dtype, op: str, variant) -> None:
@@ -223,6 +224,12 @@ def set_variant(N: int, dtype: torch.dtype, op: str, variant) -> None:
 
 def get_variant(N: int, dtype: torch.dtype, op: str) -> int:
     return int(_lib.load().pauli_get_variant(int(N), _DTYPES[dtype], {"decompose": 0, "compose": 1}[op]))
+
+
+def stream_status(stream: torch.cuda.Stream | None = None) -> None:
+    """Synchronise the stream and raise PauliError if a tiled launch on it timed out."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    check(_lib.load().pauli_stream_status(ctypes.c_void_p(s.cuda_stream)))
 
 
 def last_error() -> str:

@@ -1,17 +1,19 @@
 """Autotuner for libpauli's launch shapes.
 
-The XOR-diagonal kernels come in two launch shapes (include/pauli.h, PAULI_VARIANT_*):
+The XOR-diagonal kernels come in several launch shapes (include/pauli.h, PAULI_VARIANT_*):
 8192-element work units on 512-thread CTAs (one per SM) or 4096-element units on 256-thread
-CTAs (two per SM); the two differ in how the N butterfly stages split between registers,
-shared memory and the CTA cluster. The batched plan has the same two CTA shapes. Which is
+CTAs (two per SM), with 16 or 8 elements per thread, which differ in how the N butterfly
+stages split between registers, shared memory and the CTA cluster; and, for decomposition
+at N 12..14, the two-stage tiled kernel with either CTA size. The batched plan has the same two CTA shapes. Which is
 faster depends on N, the dtype and the direction, so this module times each candidate on a
 seeded synthetic input with CUDA events, keeps the fastest, applies it with
 pauli_set_variant, and stores the choices in a JSON cache keyed by the GPU's name.
 
     python -m paper_2401_16378_gb300.autotune [--out PATH] [--n 6 7 ... 14]
 
-At first use the package applies the cache named by $PAULI_AUTOTUNE_CACHE, else the file
-autotune_cache.json next to this module, when its GPU name matches the current device.
+When the library is first loaded the package applies the cache named by
+$PAULI_AUTOTUNE_CACHE, else the file autotune_cache.json next to this module, when its GPU
+name matches the current device ($PAULI_AUTOTUNE=0 turns this off).
 """
 from __future__ import annotations
 
@@ -28,7 +30,8 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotu
 _DT = {"c128": torch.complex128, "c64": torch.complex64}
 _DT_CODE = {"c128": _lib.PAULI_C128, "c64": _lib.PAULI_C64}
 _OPS = {"decompose": 0, "compose": 1}
-VARIANT_RANGE = {1: (7, 15), 2: (6, 14), 3: (6, 14), 4: (7, 15)}  # variant -> supported N range
+VARIANT_RANGE = {1: (7, 15), 2: (6, 14), 3: (6, 14), 4: (7, 15), 5: (12, 14), 6: (12, 14)}  # variant -> N range
+DECOMPOSE_ONLY = {5, 6}  # the two-stage tiled variants
 
 
 def _gpu_name() -> str:
@@ -65,7 +68,7 @@ def tune_variants(Ns=range(6, 15), dtypes=("c128", "c64"), ops=("decompose", "co
             for op in ops:
                 times = {}
                 for v, (lo, hi) in VARIANT_RANGE.items():
-                    if not lo <= N <= hi:
+                    if not lo <= N <= hi or (op == "compose" and v in DECOMPOSE_ONLY):
                         continue
                     _lib.check(lib.pauli_set_variant(N, _DT_CODE[dt], _OPS[op], v))
                     if op == "decompose":

@@ -12,6 +12,7 @@
 #include "kernels.h"
 #include "pauli.h"
 #include "plan_internal.h"
+#include "tiled.h"
 
 namespace pauli {
 int static_batch_max();
@@ -151,9 +152,18 @@ int pauli_set_variant(int N, int dtype, int op, int variant) {
   if ((st = check_dtype(dtype))) return st;
   if ((st = check_n(N))) return st;
   if (op != 0 && op != 1) return fail(PAULI_ERR_ARG, "op = %d is not 0 (decompose) or 1 (compose)", op);
-  if (variant != PAULI_VARIANT_DEFAULT && !pauli::xordiag_variant_supported(variant, N))
-    return fail(PAULI_ERR_UNSUPPORTED, "variant %d has no kernel for N = %d", variant, N);
+  if (variant != PAULI_VARIANT_DEFAULT && !pauli::xordiag_variant_supported(variant, N, op == 1))
+    return fail(PAULI_ERR_UNSUPPORTED, "variant %d has no %s kernel for N = %d", variant,
+                op == 1 ? "compose" : "decompose", N);
   pauli::xordiag_set_variant(N, dtype == PAULI_C64, op == 1, variant);
+  return PAULI_OK;
+}
+
+int pauli_stream_status(void* stream) {
+  int status = 0;
+  cudaError_t e = pauli::tiled_stream_status((cudaStream_t)stream, &status);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_stream_status");
+  if (status) return fail(status, "a bounded wait in the tiled decomposition gave up");
   return PAULI_OK;
 }
 

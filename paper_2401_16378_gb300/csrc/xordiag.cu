@@ -31,6 +31,7 @@
 //  complex64: TwoSum-compensated FP32: each value is an unevaluated pair (hi, lo); every
 //    butterfly adds with TwoSum and carries the exact rounding error into lo.
 #include "kernels.h"
+#include "tiled.h"
 
 namespace pauli {
 
@@ -41,11 +42,15 @@ cudaError_t xordiag_c64_compose(int, int, const void*, long long, int, void*, cu
 
 namespace {
 
-bool variant_has(int variant, int N) {
+bool variant_has(int variant, int N, bool compose) {
   if (variant == kVariantUnit13 || variant == kVariantUnit13x8) return N >= 7 && N <= 15;
   if (variant == kVariantUnit12 || variant == kVariantUnit12x8) return N >= 6 && N <= 14;
+  if (variant == kVariantTiled13 || variant == kVariantTiled12) return !compose && tiled_supported(N);
   return false;
 }
+
+// The tiled kernel numbers its work items with 32-bit integers.
+constexpr long long kTiledMaxCount = 1024;
 
 // Chosen variant per (N, dtype, direction): 0 = built-in default. Set by the autotuner.
 int g_variant[2][2][17];
@@ -56,7 +61,7 @@ int default_variant(int N) { return N >= 7 ? kVariantUnit13 : kVariantUnit12; }
 
 bool xordiag_supported(int N) { return N >= 6 && N <= 15; }
 
-bool xordiag_variant_supported(int variant, int N) { return variant_has(variant, N); }
+bool xordiag_variant_supported(int variant, int N, bool compose) { return variant_has(variant, N, compose); }
 
 int xordiag_get_variant(int N, bool c64, bool compose) {
   if (N < 0 || N > 16) return 0;
@@ -70,8 +75,16 @@ void xordiag_set_variant(int N, bool c64, bool compose, int variant) {
 
 cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, bool compose, int scale_exp, void* out,
                            cudaStream_t s, int variant) {
-  if (!variant) variant = xordiag_get_variant(N, c64, compose);
-  if (!variant_has(variant, N)) return cudaErrorNotSupported;
+  if (!variant) {
+    variant = xordiag_get_variant(N, c64, compose);
+    if ((variant == kVariantTiled13 || variant == kVariantTiled12) && count > kTiledMaxCount)
+      variant = default_variant(N);
+  }
+  if (!variant_has(variant, N, compose)) return cudaErrorNotSupported;
+  if (variant == kVariantTiled13 || variant == kVariantTiled12) {
+    if (count > kTiledMaxCount) return cudaErrorNotSupported;
+    return launch_tiled(in, N, (int)count, c64, out, variant == kVariantTiled13 ? 13 : 12, s);
+  }
   if (c64)
     return compose ? xordiag_c64_compose(variant, N, in, count, scale_exp, out, s)
                    : xordiag_c64_decompose(variant, N, in, count, scale_exp, out, s);

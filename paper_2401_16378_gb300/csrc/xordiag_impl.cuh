@@ -241,15 +241,31 @@ struct ArC128 {
   __device__ static __forceinline__ Elem unpack(const uint4& q) {
     return Elem{(long long)(((unsigned long long)q.y << 32) | q.x), (long long)(((unsigned long long)q.w << 32) | q.z)};
   }
-  // Store W * 2^scale * i^k.
-  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+  // W * 2^scale * i^k as a double pair.
+  __device__ static __forceinline__ double2 out_value(const Elem& a, const Conv& cv, uint32_t k) {
     const bool swap = k & 1u;
     const long long x = swap ? a.im : a.re, y = swap ? a.re : a.im;
     double2 o;
     o.x = from_fixed(x, cv, (k ^ (k >> 1)) & 1u);
     o.y = from_fixed(y, cv, (k >> 1) & 1u);
     if (cv.nan) o.x = o.y = f64_nan();
-    reinterpret_cast<double2*>(p)[i] = o;
+    return o;
+  }
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    reinterpret_cast<double2*>(p)[i] = out_value(a, cv, k);
+  }
+  // Same, with an L2 cache policy (createpolicy) for the store.
+  __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
+                                                    uint32_t k, uint64_t pol) {
+    const double2 o = out_value(a, cv, k);
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(reinterpret_cast<double2*>(p) + i),
+                 "d"(o.x), "d"(o.y), "l"(pol)
+                 : "memory");
+  }
+  // Arithmetic right shift by sh in [0, 63]: re-expresses a value held at scale 2^s at 2^(s - sh).
+  __device__ static __forceinline__ void align(Elem& a, int sh) {
+    a.re >>= sh;
+    a.im >>= sh;
   }
 };
 
@@ -303,11 +319,22 @@ struct ArC64 {
   __device__ static __forceinline__ Elem unpack(const uint4& q) {
     return Elem{__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), __uint_as_float(q.w)};
   }
-  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+  __device__ static __forceinline__ float2 out_value(const Elem& a, const Conv& cv, uint32_t k) {
     float re = __fadd_rn(a.rh, a.rl), im = __fadd_rn(a.ih, a.il);
     mul_i_pow(re, im, k);
-    reinterpret_cast<float2*>(p)[i] = make_float2(__fmul_rn(re, cv.scale), __fmul_rn(im, cv.scale));
+    return make_float2(__fmul_rn(re, cv.scale), __fmul_rn(im, cv.scale));
   }
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    reinterpret_cast<float2*>(p)[i] = out_value(a, cv, k);
+  }
+  __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
+                                                    uint32_t k, uint64_t pol) {
+    const float2 o = out_value(a, cv, k);
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1,%2}, %3;" ::"l"(reinterpret_cast<float2*>(p) + i),
+                 "f"(o.x), "f"(o.y), "l"(pol)
+                 : "memory");
+  }
+  __device__ static __forceinline__ void align(Elem&, int) {}
 };
 
 // Butterflies over the low G register-index bits.

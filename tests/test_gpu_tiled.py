@@ -1,0 +1,132 @@
+"""GPU parity of the two-stage tiled decomposition (PAULI_VARIANT_TILED8192 / TILED4096).
+
+Stage 1 transforms 64 XY-masks x 2^TB rows per tile with a per-(class, tile) fixed-point
+scale, stage 2 re-scales the tiles of each class to the class maximum and finishes the
+transform. Checked against the oracle on sampled coefficients (random and special indices),
+bit for bit on integer-valued inputs (every partial sum is exact on both sides, including
+the re-scaling shift), on inputs whose tiles differ by many binades (the re-scaling path),
+with all-zero tiles, with a non-finite entry, on a batch, and on repeated launches that reuse
+the scratch ring. Tolerances as in test_gpu_parity: 1e-12 max|G| (complex128), 2e-6 max|G|
+(complex64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2401_16378_gb300 as pg
+from paper_2401_16378_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.complex128: 1e-12, torch.complex64: 2e-6}
+NP = {torch.complex128: np.complex128, torch.complex64: np.complex64}
+TILED = ("tiled8192", "tiled4096")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def run_tiled(Gd, N, dtype, variant):
+    pg.set_variant(N, dtype, "decompose", variant)
+    try:
+        c = pg.decompose(Gd, method="xordiag")
+        pg.stream_status()
+        return host(c)
+    finally:
+        pg.set_variant(N, dtype, "decompose", "default")
+
+
+def assert_close(got, want, scale, dtype):
+    err = np.max(np.abs(got.astype(np.complex128) - want))
+    assert err <= TOL[dtype] * scale, f"err {err:.3e} > {TOL[dtype]:.0e} * {scale:.3e}"
+
+
+@pytest.mark.parametrize("variant", TILED)
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("N", [12, 13, 14])
+def test_tiled_matches_oracle_and_single_pass(N, dtype, variant):
+    G = workloads.gaussian_complex(N, 2000 + N)
+    Gd = dev(G.astype(NP[dtype]))
+    got = run_tiled(Gd, N, dtype, variant)
+    idx = workloads.sample_indices(N, 2100 + N, k=1024)
+    ref = G.astype(NP[dtype]).astype(np.complex128)
+    assert_close(got[idx.astype(np.int64)], oracle.decompose_at(ref, idx), np.max(np.abs(G)), dtype)
+    # every coefficient against the single-pass kernel (itself held to the oracle elsewhere)
+    single = host(pg.decompose(Gd, method="xordiag"))
+    assert_close(got, single.astype(np.complex128), 2 * np.max(np.abs(G)), dtype)
+
+
+@pytest.mark.parametrize("variant", TILED)
+@pytest.mark.parametrize("N", [12, 14])
+def test_tiled_integer_input_bit_exact(N, variant):
+    G = workloads.integer_complex(N, 2200 + N)
+    got = run_tiled(dev(G), N, torch.complex128, variant)
+    idx = workloads.sample_indices(N, 2300 + N, k=1024)
+    np.testing.assert_array_equal(got[idx.astype(np.int64)], oracle.decompose_at(G, idx))
+
+
+@pytest.mark.parametrize("variant", TILED)
+def test_tiled_rescaling_across_binades_and_zero_tiles(variant):
+    """Row blocks scaled by 2^e, e in [-60, 60], and some all-zero: each class's tiles sit at
+    different fixed-point scales, and zero tiles carry exponent key 0."""
+    N = 13
+    G = workloads.gaussian_complex(N, 2400)
+    rng = np.random.default_rng(2401)
+    blocks = G.reshape(1 << (N - 6), 64, 1 << N)  # 64-row bands (tiles of both variants nest in them)
+    e = rng.integers(-60, 61, size=blocks.shape[0])
+    blocks *= (2.0 ** e)[:, None, None]
+    blocks[rng.choice(blocks.shape[0], 9, replace=False)] = 0
+    got = run_tiled(dev(G), N, torch.complex128, variant)
+    idx = workloads.sample_indices(N, 2402, k=1024)
+    assert_close(got[idx.astype(np.int64)], oracle.decompose_at(G, idx), np.max(np.abs(G)), torch.complex128)
+
+
+def test_tiled_nonfinite_entry_gives_nan_for_its_mask_only():
+    N = 12
+    G = workloads.gaussian_complex(N, 2500)
+    G[700, 3001] = np.inf
+    got = run_tiled(dev(G), N, torch.complex128, "tiled8192")
+    n_all = np.arange(4 ** N, dtype=np.int64)
+    even = np.zeros_like(n_all)
+    odd = np.zeros_like(n_all)
+    for t in range(N):
+        even |= ((n_all >> (2 * t)) & 1) << t
+        odd |= ((n_all >> (2 * t + 1)) & 1) << t
+    mask = (even ^ odd) == (700 ^ 3001)
+    assert np.all(np.isnan(got[mask]))
+    assert not np.any(np.isnan(got[~mask]))
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_tiled_batch_and_repeated_launches(dtype):
+    """count = 3 matrices in one launch (blocks of later matrices reuse ring slots), then the
+    same launch twice more: identical results every time."""
+    N = 12
+    Gs = np.stack([workloads.gaussian_complex(N, 2600 + b) for b in range(3)]).astype(NP[dtype])
+    Gd = dev(Gs)
+    pg.set_variant(N, dtype, "decompose", "tiled8192")
+    try:
+        outs = [host(pg.decompose(Gd, method="xordiag")) for _ in range(3)]
+        pg.stream_status()
+    finally:
+        pg.set_variant(N, dtype, "decompose", "default")
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    idx = workloads.sample_indices(N, 2601, k=256)
+    for b in range(3):
+        ref = Gs[b].astype(np.complex128)
+        assert_close(outs[0][b][idx.astype(np.int64)], oracle.decompose_at(ref, idx), np.max(np.abs(ref)), dtype)
+
+
+def test_tiled_variant_is_decompose_only():
+    with pytest.raises(pg.PauliError, match="UNSUPPORTED"):
+        pg.set_variant(14, torch.complex128, "compose", "tiled8192")
+    with pytest.raises(pg.PauliError, match="UNSUPPORTED"):
+        pg.set_variant(11, torch.complex128, "decompose", "tiled8192")
