@@ -144,17 +144,19 @@ void pauli_plan_destroy(pauli_plan* plan);
  *                           per SM), N 6..14.
  * PAULI_VARIANT_UNIT8192X8: 8192-element work units, 1024-thread CTAs (8 per thread), N 7..15.
  * For N above 12 (resp. 11) a unit is one pair of XY-masks spread over a CTA cluster.
- * PAULI_VARIANT_TILED8192:  decomposition only, N 12..14, count <= 1024: two stages through a
- *                           library-owned scratch ring that stays in L2. Stage 1 reads tiles of
- *                           64 XY-masks x 128 rows (each row a contiguous 64-element run of G)
- *                           and does the 7 low transform stages; stage 2 the other N - 7. One
- *                           persistent launch of 512-thread CTAs. The scratch (3 x 2^(N+10)
- *                           bytes plus 256) is allocated with cudaMalloc at the first call on
- *                           each (device, stream) pair and kept until the process exits: make
- *                           that first call before capturing the stream into a graph. Calls on
- *                           one stream are ordered by the stream; calls on different streams
- *                           get different scratch.
- * PAULI_VARIANT_TILED4096:  the same with 64 x 64-row tiles on 256-thread CTAs, two per SM.
+ * PAULI_VARIANT_TILED8:     decomposition only, N 12..14, count <= 1024, G 16-byte aligned:
+ *                           two stages through a library-owned scratch ring that stays in L2.
+ *                           Stage 1 reads tiles of 64 XY-masks x 64 rows (each row a contiguous
+ *                           64-element run of G) and does the 6 low transform stages; stage 2
+ *                           the other N - 6. One persistent, warp-specialised launch (a copy
+ *                           warp feeding 512 compute threads, 8 elements each, through a ring
+ *                           of shared-memory buffers). The scratch (3 x 2^(N+10) bytes plus
+ *                           about 1 MiB) is allocated with cudaMalloc at the first call on each
+ *                           (device, stream) pair and kept until the process exits: make that
+ *                           first call before capturing the stream into a graph. Calls on one
+ *                           stream are ordered by the stream; calls on different streams get
+ *                           different scratch.
+ * PAULI_VARIANT_TILED16:    the same with 256 compute threads of 16 elements each.
  * All variants compute bit-identical complex128 results, except that the tiled ones re-scale
  * partial sums between the stages (an extra truncation below the class quantum, well inside
  * the accuracy bound of pauli_decompose); they differ otherwise only in speed. The choice is process-wide per (N, dtype, op), op 0 =
@@ -165,8 +167,8 @@ void pauli_plan_destroy(pauli_plan* plan);
 #define PAULI_VARIANT_UNIT4096 2
 #define PAULI_VARIANT_UNIT4096X8 3
 #define PAULI_VARIANT_UNIT8192X8 4
-#define PAULI_VARIANT_TILED8192 5
-#define PAULI_VARIANT_TILED4096 6
+#define PAULI_VARIANT_TILED8 5
+#define PAULI_VARIANT_TILED16 6
 int pauli_set_variant(int N, int dtype, int op, int variant);
 /* The variant in effect for (N, dtype, op), or 0 when PAULI_XORDIAG has none for N. */
 int pauli_get_variant(int N, int dtype, int op);

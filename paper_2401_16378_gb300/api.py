@@ -212,8 +212,8 @@ def decompose_autograd(G: torch.Tensor, method="auto") -> torch.Tensor:
     return PauliDecompose.apply(G, method)
 
 
-VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4, "tiled8192": 5,
-            "tiled4096": 6}
+VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4, "tiled8": 5,
+            "tiled16": 6}
 
 
 def set_variant(N: int, dtype: torch.dtype, op: str, variant) -> None:

@@ -20,8 +20,8 @@ constexpr int kVariantUnit13 = 1;    // 8192-element units, 512 threads x 16 ele
 constexpr int kVariantUnit12 = 2;    // 4096-element units, 256 threads x 16 elements, 2 CTAs/SM
 constexpr int kVariantUnit12x8 = 3;  // 4096-element units, 512 threads x 8 elements, 2 CTAs/SM
 constexpr int kVariantUnit13x8 = 4;  // 8192-element units, 1024 threads x 8 elements
-constexpr int kVariantTiled13 = 5;   // two-stage tiled decomposition (tiled.cu), 512-thread CTAs
-constexpr int kVariantTiled12 = 6;   // two-stage tiled decomposition, 256-thread CTAs, 2 per SM
+constexpr int kVariantTiled8 = 5;    // two-stage tiled decomposition (tiled.cu), 512 consumers x 8 elements
+constexpr int kVariantTiled16 = 6;   // two-stage tiled decomposition, 256 consumers x 16 elements
 bool xordiag_supported(int N);
 bool xordiag_variant_supported(int variant, int N, bool compose);
 int xordiag_get_variant(int N, bool c64, bool compose);

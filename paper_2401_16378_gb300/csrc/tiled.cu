@@ -1,6 +1,6 @@
 // tiled.cu -- host side of the two-stage tiled decomposition: the scratch workspace per
 // (device, stream), dispatch to the per-shape instantiations, and the status word.
-// The kernels and the algorithm are in tiled_impl.cuh.
+// The kernel and the algorithm are in tiled_impl.cuh.
 #include <cstddef>
 #include <mutex>
 #include <vector>
@@ -9,10 +9,10 @@
 
 namespace pauli {
 
-cudaError_t tiled_launch_c128_u13(const void*, int, int, void*, cudaStream_t);
-cudaError_t tiled_launch_c128_u12(const void*, int, int, void*, cudaStream_t);
-cudaError_t tiled_launch_c64_u13(const void*, int, int, void*, cudaStream_t);
-cudaError_t tiled_launch_c64_u12(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_c128_r3(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_c128_r4(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_c64_r3(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_c64_r4(const void*, int, int, void*, cudaStream_t);
 
 namespace {
 
@@ -61,12 +61,10 @@ cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out) {
 
 bool tiled_supported(int N) { return N >= 12 && N <= 14; }
 
-cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int unit_bits, cudaStream_t st) {
+cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st) {
   if (!tiled_supported(N)) return cudaErrorNotSupported;
-  if (unit_bits == 13)
-    return c64 ? tiled_launch_c64_u13(G, N, count, out, st) : tiled_launch_c128_u13(G, N, count, out, st);
-  if (unit_bits == 12)
-    return c64 ? tiled_launch_c64_u12(G, N, count, out, st) : tiled_launch_c128_u12(G, N, count, out, st);
+  if (rb == 3) return c64 ? tiled_launch_c64_r3(G, N, count, out, st) : tiled_launch_c128_r3(G, N, count, out, st);
+  if (rb == 4) return c64 ? tiled_launch_c64_r4(G, N, count, out, st) : tiled_launch_c128_r4(G, N, count, out, st);
   return cudaErrorNotSupported;
 }
 

@@ -1,28 +1,32 @@
-// tiled.h -- the two-stage XOR-diagonal decomposition for large N (tiled.cu).
+// tiled.h -- the two-stage XOR-diagonal decomposition for large N (tiled.cu, tiled_impl.cuh).
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <cstddef>
 
 namespace pauli {
 
-constexpr int kTiledSlots = 3;           // scratch ring slots
-constexpr size_t kTiledCtrlBytes = 256;  // control block, padded so the slots start 256-byte aligned
+constexpr int kTiledSlots = 3;  // scratch ring slots
 
-// Device control block at the start of the workspace; cleared before every launch except
-// `status`, which keeps the first error until pauli_stream_status reads and clears it.
+// Device control block at the start of the workspace. Everything from `counter` on is
+// cleared before every launch; `status` keeps the first error until pauli_stream_status reads
+// and clears it.
 struct TiledCtrl {
-  int counter;                 // next work item
-  int s1_done[kTiledSlots];    // stage-1 tiles completed per slot (all generations)
-  int s2_done[kTiledSlots];    // stage-2 items that have read their slot (all generations)
-  int pad;
-  int status;                  // PAULI_OK or PAULI_ERR_TIMEOUT
+  int status;  // PAULI_OK or PAULI_ERR_TIMEOUT
+  int pad0[3];
+  int counter;                  // next work item
+  int s1_done[kTiledSlots];     // stage-1 tiles completed per slot (all generations)
+  int s2_done[kTiledSlots];     // stage-2 items that have copied their slot's data (all generations)
+  int pad1[5];
+  uint32_t emax[kTiledSlots][64];  // per class of the slot's block: (generation + 1) << 11 | exponent
 };
+constexpr size_t kTiledCtrlBytes = 1024;  // control block, padded; the slots follow
+static_assert(sizeof(TiledCtrl) <= kTiledCtrlBytes, "control block fits its padding");
 
 bool tiled_supported(int N);
-// Unit size (log2 elements) of the tiled launch: 13 (512 threads, one CTA per SM) or 12 (256
-// threads, two CTAs per SM).
-cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int unit_bits, cudaStream_t st);
+// rb = log2 of the elements per consumer thread: 3 (512 consumer threads) or 4 (256).
+cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st);
 // Status word of the workspace used on `st` (synchronises st); 0 when none exists.
 cudaError_t tiled_stream_status(cudaStream_t st, int* status);
 

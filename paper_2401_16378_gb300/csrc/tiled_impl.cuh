@@ -1,5 +1,6 @@
 // tiled_impl.cuh -- kernel and launcher templates of the two-stage tiled decomposition
-// (tiled.cu), instantiated per dtype and CTA shape by tiled_c128_u13.cu and its siblings.
+// (host side in tiled.cu), instantiated per dtype and consumer shape by tiled_c128_r3.cu and
+// its siblings.
 //
 // The decomposition for 12 <= N <= 14 in two stages through an L2-resident scratch ring.
 //
@@ -7,29 +8,42 @@
 // row r: 2^K consecutive masks give a 2^K-element run per row, and on-chip capacity forces K
 // down as N grows (K = 1 from N = 12 on: 32 bytes of a 64-256 KiB row), which DRAM serves
 // far below its copy bandwidth. This path splits the transform of Eq. (13) over the row
-// index r = (R, i), R = r >> TB, i = r & (2^TB - 1), TB = UB - 6:
+// index r = (R, i), R = r >> 6, i = r & 63:
 //
-//  stage 1, per block of 64 XY-masks x = 64k + c and tile of 2^TB rows R: the elements
-//    G[2^TB R + i, (2^TB R + i) ^ x] form a 2^TB x 64 block of G (each row one contiguous
-//    run of 64 elements), and the tile's 64 classes get their TB low WHT stages (over i):
-//        P[x][R][w] = sum_i (-1)^popc(i & w) e_x[2^TB R + i],   w < 2^TB,
+//  stage 1, per block of 64 XY-masks x = 64k + c and tile of 64 rows R: the elements
+//    G[64R + i, (64R + i) ^ x] are the 64 x 64 submatrix of G at rows 64R.., columns
+//    (64R ^ 64k).. (element (i, c) at column offset i ^ c), whose rows are contiguous 64-element
+//    runs; the tile's 64 classes get their 6 low WHT stages (over i):
+//        P[x][R][w] = sum_i (-1)^popc(i & w) e_x[64R + i],   w < 64,
 //    in int64 fixed point with a per-(class, tile) scale (complex128), or as TwoSum pairs
 //    (complex64), stored to a scratch slot together with the scale.
-//  stage 2, per 8 classes and a group of w: the remaining N - TB stages over R,
-//        W_x[(h << TB) | w] = sum_R (-1)^popc(R & h) P[x][R][w],
-//    after re-scaling every tile to its class's largest scale (an exact arithmetic right
-//    shift: a tile at a finer scale drops bits below the class quantum), then the phase
-//    i^popc(x&z), the 2^-N scale and the store of c(x, z) in the paper's order (Eq. (2)).
+//  stage 2, per 8 classes (an octet) and a group of 2^ZB values of w: the remaining L = N - 6
+//    stages over R,
+//        W_x[(h << 6) | w] = sum_R (-1)^popc(R & h) P[x][R][w],
+//    after re-scaling every tile to its class's largest scale (an arithmetic right shift: a
+//    tile at a finer scale drops bits below the class quantum), then the phase i^popc(x&z),
+//    the 2^-N scale and the store of c(x, z) in the paper's order (Eq. (2)).
 //
-// One persistent launch runs both stages from a single work counter, in the order
-// S1(block 0), S1(1), S2(0), S1(2), S2(1), ...; the scratch is a ring of kTiledSlots slots of
-// 64 x 2^N partials (16 MiB at N = 14), stored with an L2 evict-last policy so that it stays in
-// L2, while G and c stream with evict-first. A stage-2 item waits until the 2^(N-TB) tiles of
-// its block are complete, and a stage-1 item waits until the stage-2 items of the block that
-// last used its slot have read it. Every item waited on was taken from the counter earlier by
-// a CTA that is already running and finishes it without waiting on any later item, so all
-// waits end; they are bounded anyway: after kPolls polls the waiting CTA records
-// PAULI_ERR_TIMEOUT in the status word and carries on (its results are then not valid).
+// The scratch is laid out so that each stage-2 item reads one contiguous 64 KiB chunk:
+// P[o][q][R][wl][c8] (octet o, w = (q << ZB) | wl, class 8o + c8), 16 bytes per entry,
+// then E[o][R][c8] (exponent key of each class in each tile). A ring of kTiledSlots slots
+// holds 64 x 2^N partials each (16 MiB at N = 14); it is written with an L2 evict-last policy
+// and stays in L2 while G and c stream through with evict-first.
+//
+// Launch: one persistent CTA per SM, warp-specialised. A producer warp takes work items from
+// a global counter in the order S1(block 0), S1(1), S2(0), S1(2), S2(1), ..., waits for the
+// item's dependencies (a stage-2 item needs the 2^L tiles of its block; a stage-1 item needs
+// the stage-2 items of the block that last used its slot to have copied their data out), and
+// fills a 3-deep ring of shared-memory buffers with cp.async.bulk copies (64 row runs of 1 KiB
+// for a tile of complex128 G, one chunk for a stage-2 item) that complete on an mbarrier. The
+// consumer warps (512 threads x 8 elements or 256 x 16) take the buffers in order, compute,
+// store, publish completion with a release reduction and hand the buffer back. Loads for the
+// next two items are thus in flight while one is computed.
+//
+// Every item waited on was taken from the counter earlier by a CTA that processes its items in
+// the order it took them, so every wait ends. Each wait is bounded nevertheless: after
+// kPolls polls the waiting thread records PAULI_ERR_TIMEOUT in the status word, the CTA stops
+// taking work, waits (bounded) for its copies in flight and exits; the results are then invalid.
 #pragma once
 #include <cstddef>
 
@@ -46,10 +60,33 @@ namespace tiled {
 namespace {
 using namespace xd;
 
-constexpr int kCB = 6;  // class bits per block
-constexpr int kPolls = 1 << 22;
+constexpr int kCB = 6;             // class bits per block
+constexpr int kUB = 12;            // log2 elements per item
+constexpr int kTB = kUB - kCB;     // log2 rows per stage-1 tile
+constexpr int kBufs = 3;           // shared-memory ring depth
+constexpr int kPolls = 1 << 24;    // bound of every wait loop (each poll sleeps or blocks briefly)
 constexpr int kStatusTimeout = 8;  // PAULI_ERR_TIMEOUT
 
+template <int N>
+struct Geo {
+  static constexpr int L = N - kTB;        // stage-2 bits (row blocks)
+  static constexpr int K2 = kUB - L;       // stage-2 class bits: 3 (octet) + ZB (w)
+  static constexpr int ZB = K2 - 3;
+  static constexpr int NR = 1 << L;        // tiles per block
+  static constexpr int NQ = 1 << (kTB - ZB);  // w groups per octet
+  static constexpr int n1 = NR;            // stage-1 items per block
+  static constexpr int n2 = 8 * NQ;        // stage-2 items per block
+  static constexpr size_t kChunk = (size_t)16 << kUB;          // bytes per item (64 KiB)
+  static constexpr size_t kEOct = (size_t)NR * 8 * 4;          // E bytes per octet
+  static constexpr size_t kBuf = kChunk + kEOct + 128;         // buffer: data, E, class maxima
+  static constexpr size_t kSlotP = (size_t)16 << (N + kCB);
+  static constexpr size_t kSlot = kSlotP + (size_t)NR * 64 * 4;
+  static constexpr size_t kWorkspace = kTiledCtrlBytes + kTiledSlots * kSlot;
+  static_assert(ZB >= 0 && L >= 4, "12 <= N <= 15");
+  static_assert(n1 == n2, "both stages have 2^L items per block");
+};
+
+// ------------------------------------------------------------------- PTX helpers --
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
@@ -60,36 +97,7 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-// G is read once: no L1 allocation, evict-first in L2
-template <class Raw>
-__device__ __forceinline__ Raw ld_stream(const void* base, unsigned long long i, uint64_t pol);
-template <>
-__device__ __forceinline__ uint4 ld_stream<uint4>(const void* base, unsigned long long i, uint64_t pol) {
-  uint4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(reinterpret_cast<const uint4*>(base) + i), "l"(pol));
-  return v;
-}
-template <>
-__device__ __forceinline__ float2 ld_stream<float2>(const void* base, unsigned long long i, uint64_t pol) {
-  float2 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;"
-               : "=f"(v.x), "=f"(v.y)
-               : "l"(reinterpret_cast<const float2*>(base) + i), "l"(pol));
-  return v;
-}
-// Scratch reads: written by other CTAs during this launch, so through L2 only (.cg), never the
-// non-coherent path.
-__device__ __forceinline__ uint4 ld_scratch(const uint4* a, uint64_t pol) {
-  uint4 v;
-  asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(a), "l"(pol)
-               : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_hint(uint4* a, const uint4& v, uint64_t pol) {
+__device__ __forceinline__ void st_hint(void* a, const uint4& v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(a), "r"(v.x), "r"(v.y), "r"(v.z),
                "r"(v.w), "l"(pol)
                : "memory");
@@ -99,269 +107,409 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-
-// Thread 0 polls until *counter >= target (bounded), then the whole CTA proceeds.
-__device__ __forceinline__ void wait_for(const int* counter, int target, int* status) {
-  if (threadIdx.x == 0) {
-    int i = 0;
-    while (ld_acquire(counter) < target) {
-      if (++i == kPolls) {
-        atomicExch(status, kStatusTimeout);
-        break;
-      }
-      __nanosleep(256);
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// All threads' prior accesses are ordered before the increment (barrier, then a fence by
-// the thread that increments).
-__device__ __forceinline__ void signal(int* counter) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(counter, 1);
-  }
+__device__ __forceinline__ void red_max(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared bulk copy completing on mbarrier `bar` (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
 }
 
-// Scratch slot s: P[R][w][c] (16 bytes each: the int64 pair of complex128, or the two TwoSum
-// float pairs of complex64), then E[R][c] (exponent key of each class in each tile).
-struct Slot {
-  uint4* P;
-  uint32_t* E;
+// Shared state of one CTA.
+struct Shared {
+  uint64_t full[kBufs];   // buffer filled (producer arrival + copied bytes)
+  uint64_t empty[kBufs];  // buffer released by the consumers
+  int item[kBufs];        // work item in the buffer, -1 = no more work
+  int abort;              // a wait of the producer gave up: stop
+  int ok;                 // consumers: the next buffer arrived (broadcast by consumer 0)
+  int consumed;           // buffer uses completed by the consumers
+  int issued;             // buffer uses whose copies the producer has issued
+  uint32_t smax[64];      // stage 1: (use + 1) << 11 | largest exponent of each class
 };
-__host__ __device__ constexpr size_t slot_p_elems(int N) { return ((size_t)1 << N) << kCB; }
-__host__ __device__ constexpr size_t slot_bytes(int N, int TB) {
-  return slot_p_elems(N) * 16 + ((((size_t)1 << (N - TB)) << kCB) * 4 + 255) / 256 * 256;
+
+// Bounded wait on an mbarrier phase; false (status recorded) when it gave up.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, int* status) {
+  for (int i = 0; i < kPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(status, kStatusTimeout);
+  return false;
 }
-__device__ __forceinline__ Slot slot_of(TiledCtrl* ws, int N, int TB, int s) {
-  char* base = reinterpret_cast<char*>(ws) + kTiledCtrlBytes + (size_t)s * slot_bytes(N, TB);
-  return Slot{reinterpret_cast<uint4*>(base), reinterpret_cast<uint32_t*>(base + slot_p_elems(N) * 16)};
+// Bounded wait until *counter >= target (one thread); false (status recorded) when it gave up.
+__device__ __forceinline__ bool wait_count(const int* counter, int target, int* status) {
+  for (int i = 0; i < kPolls; ++i) {
+    if (ld_acquire(counter) >= target) return true;
+    __nanosleep(128);
+  }
+  atomicExch(status, kStatusTimeout);
+  return false;
 }
 
-// ---------------------------------------------------------------------------- stage 1 --
-// Tile R of block k: rows [2^TB R, 2^TB (R+1)), classes [64k, 64k + 64).
-template <int UB, int N, class AR>
-__device__ __forceinline__ void stage1(const void* __restrict__ G, unsigned long long gbase, uint32_t k, uint32_t R,
-                                       const Slot& sl, uint32_t xaddr, uint32_t* smax, uint64_t pol_in,
-                                       uint64_t pol_keep) {
-  constexpr int TB = UB - kCB;
-  using LY = Layout<UB, TB, 4>;
-  static_assert(LY::K == kCB, "tile = 64 classes x 2^TB rows");
-  constexpr int E = LY::E, LAST = LY::NPH - 1;
+// Work item -> (stage, block, index within the block); false for the padding items of the
+// order (stage 1 past the last block, stage 2 before the first).
+template <int N>
+struct Item {
+  bool s1;
+  int b, j;
+  __device__ __forceinline__ bool decode(int item, int blocks) {
+    constexpr int group = Geo<N>::n1 + Geo<N>::n2;
+    const int g = item / group, r = item % group;
+    s1 = r < Geo<N>::n1;
+    b = s1 ? g : g - 1;
+    j = s1 ? r : r - Geo<N>::n1;
+    return s1 ? g < blocks : g > 0;
+  }
+};
+
+__device__ __forceinline__ char* slot_base(TiledCtrl* ws, size_t slot_bytes, int s) {
+  return reinterpret_cast<char*>(ws) + kTiledCtrlBytes + (size_t)s * slot_bytes;
+}
+
+// ---------------------------------------------------------------------- producer --
+template <int N, class AR>
+__device__ void producer(const void* __restrict__ G, int count, TiledCtrl* ws, Shared& sh, uint32_t buf0) {
+  using GE = Geo<N>;
   constexpr uint32_t D = 1u << N;
+  constexpr int nb = 1 << (N - kCB);
+  constexpr uint32_t kRowBytes = 64u * sizeof(typename AR::Raw);
+  const int lane = threadIdx.x & 31;
+  const int blocks = nb * count;
+  const int n_items = (blocks + 1) * (GE::n1 + GE::n2);
+  const uint64_t pol_first = policy_evict_first();
+  int next = 0;
+  if (lane == 0) next = atomicAdd(&ws->counter, 1);
+  next = __shfl_sync(0xFFFFFFFFu, next, 0);
+  int use = 0;
+  for (;;) {
+    const int item = next;
+    const bool done = item >= n_items;
+    Item<N> it;
+    bool real = false;
+    if (!done) {
+      if (lane == 0) next = atomicAdd(&ws->counter, 1);  // latency overlaps the rest of this item
+      next = __shfl_sync(0xFFFFFFFFu, next, 0);
+      real = it.decode(item, blocks);
+      if (!real) continue;
+    }
+    const int buf = use % kBufs;
+    const uint32_t full = (uint32_t)__cvta_generic_to_shared(&sh.full[buf]);
+    const uint32_t empty = (uint32_t)__cvta_generic_to_shared(&sh.empty[buf]);
+    bool ok = true;
+    if (lane == 0 && use >= kBufs) ok = wait_phase(empty, ((use / kBufs) - 1) & 1, &ws->status);
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    if (!ok) {  // the consumers never released the buffer: they time out on their own wait
+      if (lane == 0) sh.abort = 1;
+      break;
+    }
+    const int s = done ? 0 : it.b % kTiledSlots, gen = done ? 0 : it.b / kTiledSlots;
+    if (lane == 0 && !done) {
+      // dependencies: the slot must be free (stage 1) or complete (stage 2)
+      if (it.s1) {
+        if (gen > 0) ok = wait_count(&ws->s2_done[s], GE::n2 * gen, &ws->status);
+      } else {
+        ok = wait_count(&ws->s1_done[s], GE::n1 * (gen + 1), &ws->status);
+        // the chunk was written through the generic proxy; the copy reads it through the async one
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+      }
+    }
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    if (done || !ok) {  // no more work (or a dependency never came): tell the consumers
+      if (lane == 0) {
+        if (!ok) sh.abort = 1;
+        sh.item[buf] = -1;
+        mbar_arrive(full);
+      }
+      break;
+    }
+    const uint32_t dst = buf0 + (uint32_t)(buf * GE::kBuf);
+    if (lane == 0) {
+      sh.item[buf] = item;
+      const uint32_t bytes = it.s1 ? kRowBytes * 64u : (uint32_t)(GE::kChunk + GE::kEOct + 32);
+      mbar_arrive_tx(full, bytes);
+    }
+    __syncwarp();
+    if (it.s1) {
+      const uint32_t k = (uint32_t)(it.b % nb), R = (uint32_t)it.j;
+      const uint32_t row0 = R << kTB, colb = (row0 ^ (k << kCB)) & ~63u;
+      const char* base = reinterpret_cast<const char*>(G) +
+                         (size_t)(it.b / nb) * D * D * sizeof(typename AR::Raw);
+      for (int r = lane; r < 64; r += 32)
+        bulk_g2s(dst + (uint32_t)r * kRowBytes,
+                 base + ((size_t)(row0 + r) * D + colb) * sizeof(typename AR::Raw), kRowBytes, full, pol_first);
+    } else if (lane == 0) {
+      const uint32_t o = (uint32_t)it.j & 7u, q = (uint32_t)it.j >> 3;
+      char* sb = slot_base(ws, GE::kSlot, s);
+      bulk_g2s(dst, sb + (size_t)(o * GE::NQ + q) * GE::kChunk, (uint32_t)GE::kChunk, full, pol_first);
+      bulk_g2s(dst + (uint32_t)GE::kChunk, sb + GE::kSlotP + (size_t)o * GE::kEOct, (uint32_t)GE::kEOct, full,
+               pol_first);
+      bulk_g2s(dst + (uint32_t)(GE::kChunk + GE::kEOct), &ws->emax[s][o * 8], 32u, full, pol_first);
+    }
+    ++use;
+    if (lane == 0) sh.issued = use;
+  }
+}
+
+// ---------------------------------------------------------------------- stage 1 --
+// Tile R of block k from the buffer: element (i, c) at 16-byte slot (i << 6) | (i ^ c).
+template <int N, int RB, class AR, int CT>
+__device__ __forceinline__ void stage1(uint32_t tile, char* slot, TiledCtrl* ws, int s, int gen, uint32_t R,
+                                       Shared& sh, uint32_t tag, uint64_t pol_keep) {
+  using GE = Geo<N>;
+  using LY = Layout<kUB, kTB, RB>;
+  using SY = NamedSync<1, CT>;
+  static_assert(LY::K == kCB, "tile = 64 classes x 64 rows");
+  constexpr int E = LY::E, LAST = LY::NPH - 1;
+  constexpr uint32_t kEs = sizeof(typename AR::Raw);
   const uint32_t t = threadIdx.x;
   const uint32_t c = t & 63u;
-  const uint32_t row0 = R << TB;
-  const uint32_t col0 = row0 ^ (k << kCB);        // (row0 + i) ^ (64k + c) = col0 ^ i ^ c
-  const uint32_t it = LY::thread_u(0, t) >> kCB;  // thread part of the in-tile row
+  const uint32_t it = LY::thread_u(0, t) >> kCB;
   typename AR::Raw raw[E];
   uint32_t emax = 0;
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const uint32_t i = it | (LY::reg_u(0, j) >> kCB);
-    raw[j] = ld_stream<typename AR::Raw>(G, gbase + (unsigned long long)(row0 | i) * D + (col0 ^ i ^ c), pol_in);
+    const uint32_t a = tile + ((i << 6) | (i ^ c)) * kEs;
+    if constexpr (kEs == 16) {
+      raw[j] = AR::raw_unpack(lds128(a));
+    } else {
+      uint32_t x, y;
+      asm volatile("ld.shared.v2.u32 {%0,%1}, [%2];" : "=r"(x), "=r"(y) : "r"(a) : "memory");
+      raw[j] = AR::raw_unpack(make_uint4(x, y, 0u, 0u));
+    }
     emax = max(emax, AR::exp_key(raw[j]));
   }
   uint32_t Ekey = 0;
   if constexpr (AR::kScaled) {
-    if (t < 64) smax[t] = 0;
-    __syncthreads();
-    atomicMax(&smax[c], emax);  // lanes hold distinct classes: nothing to combine within a warp
-    __syncthreads();
-    Ekey = smax[c];
+    atomicMax(&sh.smax[c], (tag << 11) | (emax >> 20));  // older tags are smaller: no reset needed
+    SY::sync();
+    Ekey = (sh.smax[c] & 0x7FFu) << 20;
   }
   const typename AR::Conv cv = AR::make_conv(N, Ekey, 0);
   typename AR::Elem v[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) v[j] = AR::template convert<0>(raw[j], cv, 0u);
-  local_wht<LY, AR>(v, xaddr, t);
+  local_wht<LY, AR, 0, SY>(v, tile, t);  // the first exchange barrier also ends the tile reads
+  // P[o][q][R][wl][c8]: o = c >> 3, c8 = c & 7, w = (q << ZB) | wl
   const uint32_t wt = LY::thread_u(LAST, t) >> kCB;
+  uint4* P = reinterpret_cast<uint4*>(slot);
+  const size_t cbase = (size_t)(c >> 3) * GE::NQ * (GE::kChunk / 16) + (c & 7u);
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const uint32_t w = wt | (LY::reg_u(LAST, j) >> kCB);
-    st_hint(sl.P + ((size_t)(row0 | w) << kCB) + c, AR::pack(v[j]), pol_keep);
+    const uint32_t q = w >> GE::ZB, wl = w & ((1u << GE::ZB) - 1u);
+    st_hint(P + cbase + (size_t)q * (GE::kChunk / 16) + (((R << GE::ZB) | wl) << 3), AR::pack(v[j]), pol_keep);
   }
-  if constexpr (AR::kScaled) {
-    if (t < 64) sl.E[(R << kCB) | t] = Ekey;
-  }
-}
-
-// L2 prefetch of tile R of block k (the rows' 64-element runs).
-template <int UB, int N, class AR>
-__device__ __forceinline__ void stage1_prefetch(const void* G, unsigned long long gbase, uint32_t k, uint32_t R) {
-  constexpr int TB = UB - kCB;
-  constexpr uint32_t D = 1u << N;
-  constexpr int kLineElems = 128 / (int)sizeof(typename AR::Raw);
-  constexpr int kPerRow = 64 / kLineElems;
-  constexpr int kLines = kPerRow << TB;  // 128-byte lines in the tile
-  const char* base = reinterpret_cast<const char*>(G);
-  for (int l = threadIdx.x; l < kLines; l += blockDim.x) {
-    const uint32_t i = (uint32_t)l / kPerRow, part = (uint32_t)l % kPerRow;
-    const uint32_t row = (R << TB) | i;
-    const uint32_t col = ((row ^ (k << kCB)) & ~63u) + part * kLineElems;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (gbase + (unsigned long long)row * D + col) *
-                                                            sizeof(typename AR::Raw)));
+  if (t < 64) {
+    uint32_t* Ep = reinterpret_cast<uint32_t*>(slot + GE::kSlotP);
+    Ep[((t >> 3) * GE::NR + R) * 8 + (t & 7u)] = Ekey;
+    if constexpr (AR::kScaled) red_max(&ws->emax[s][t], ((uint32_t)(gen + 1) << 11) | (Ekey >> 20));
   }
 }
 
-// ---------------------------------------------------------------------------- stage 2 --
-// Item (o, q) of block k: classes 64k + 8o + [0, 8), w in [2^ZB q, 2^ZB (q+1)), all R.
-template <int UB, int N, class AR>
-__device__ __forceinline__ void stage2(void* __restrict__ out, unsigned long long obase, uint32_t k, uint32_t item,
-                                       const Slot& sl, uint32_t xaddr, uint32_t* smax, uint32_t* sexp,
-                                       int* s2_counter, uint64_t pol_out, uint64_t pol_drop) {
-  constexpr int TB = UB - kCB;
-  constexpr int L = N - TB;  // row-block bits transformed here
-  using LY = Layout<UB, L, 4>;
-  constexpr int K = LY::K, E = LY::E, LAST = LY::NPH - 1;
-  constexpr int ZB = K - 3;  // log2 of the w values per item
-  static_assert(K >= 3 && L >= 4, "stage-2 unit = 8 classes x 2^ZB w x 2^L row blocks");
-  constexpr uint32_t NR = 1u << L;
+// ---------------------------------------------------------------------- stage 2 --
+// Item j = (o, q) of block k: the chunk holds entry (R, wl, c8) at 16-byte slot
+// (R << K2) | (wl << 3) | c8 -- the unit's own element order -- then E[R][c8], then the
+// eight tagged class maxima.
+template <int N, int RB, class AR, int CT>
+__device__ __forceinline__ void stage2(uint32_t chunk, const char* chunk_gen, void* __restrict__ out,
+                                       unsigned long long obase, uint32_t k, uint32_t item, uint64_t pol_out) {
+  using GE = Geo<N>;
+  using LY = Layout<kUB, GE::L, RB>;
+  using SY = NamedSync<1, CT>;
+  constexpr int K = LY::K, E = LY::E, LAST = LY::NPH - 1, ZB = GE::ZB;
+  static_assert(K == GE::K2, "stage-2 unit = 8 classes x 2^ZB w x 2^L row blocks");
   const uint32_t t = threadIdx.x;
   const uint32_t o = item & 7u, q = item >> 3;
-  const uint32_t c8 = t & 7u;                         // class within the octet (lowest thread bits)
+  const uint32_t c8 = t & 7u;
   const uint32_t w = (q << ZB) | ((t >> 3) & ((1u << ZB) - 1u));
-  const uint32_t cls = (o << 3) | c8;                 // class within the block
-  const uint32_t Rt = LY::thread_u(0, t) >> K;        // thread part of the row block
+  const uint32_t x = (k << kCB) | (o << 3) | c8;
+  const uint32_t u0 = LY::thread_u(0, t);
   typename AR::Elem v[E];
 #pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const uint32_t Rb = Rt | (LY::reg_u(0, j) >> K);
-    v[j] = AR::unpack(ld_scratch(sl.P + ((size_t)((Rb << TB) | w) << kCB) + cls, pol_drop));
-  }
-  if constexpr (AR::kScaled) {
-    // exponent keys of the octet's classes in every tile -> shared memory, and their maximum
-    if (t < 8) smax[t] = 0;
-    uint32_t m = 0;
-    for (uint32_t e = t; e < NR * 8; e += blockDim.x) {  // e & 7 == c8 (blockDim is a multiple of 8)
-      const uint32_t key = __ldcg(sl.E + (((e >> 3) << kCB) | (o << 3) | (e & 7u)));
-      sexp[e] = key;
-      m = max(m, key);
-    }
-    m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 8));
-    m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 16));
-    __syncthreads();
-    if ((t & 31u) < 8) atomicMax(&smax[c8], m);
-  }
-  signal(s2_counter);  // the slot has been read (the barrier inside also publishes smax, sexp)
+  for (int j = 0; j < E; ++j) v[j] = AR::unpack(lds128(chunk + 16u * (u0 | LY::reg_u(0, j))));
   typename AR::Conv cv;
   if constexpr (AR::kScaled) {
-    const uint32_t Emax = smax[c8];
-    cv = AR::make_conv(N, Emax, -N);
+    const uint32_t* Es = reinterpret_cast<const uint32_t*>(chunk_gen + GE::kChunk);
+    const int em = (int)(Es[GE::NR * 8 + c8] & 0x7FFu);
+    cv = AR::make_conv(N, (uint32_t)em << 20, -N);
     if (!cv.nan) {
-      const int em = (int)(Emax >> 20);
+      const uint32_t Rt = u0 >> K;
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const uint32_t Rb = Rt | (LY::reg_u(0, j) >> K);
-        // a tile at exponent et was converted at scale 2^(s + em - et): shift by em - et
-        // (0 for the largest tiles; all-zero tiles have et = 0 and hold zeros)
-        AR::align(v[j], min(em - (int)(sexp[(Rb << 3) | c8] >> 20), 63));
+        // tile at exponent et was converted at scale 2^(s + em - et): shift right by em - et
+        // (all-zero tiles have et = 0 and hold zeros)
+        AR::align(v[j], min(em - (int)(Es[(Rb << 3) | c8] >> 20), 63));
       }
     }
   } else {
     cv = AR::make_conv(N, 0u, -N);
   }
-  local_wht<LY, AR>(v, xaddr, t);
-  // c(x, z), x = 64k + cls, z = (h << TB) | w, h = ht | (register part)
-  const uint32_t x = (k << kCB) | cls;
+  local_wht<LY, AR, 0, SY>(v, chunk, t);  // the first exchange barrier also ends the chunk reads
+  // c(x, z), z = (h << 6) | w, h = ht | (register part)
   const uint32_t ht = LY::thread_u(LAST, t) >> K;
   Addr<N, false> ao;
-  ao.init(obase, x, (ht << TB) | w);
-  BitSum<LY::regrow(LAST, 0) + TB, LY::regrow(LAST, 1) + TB, LY::regrow(LAST, 2) + TB, LY::regrow(LAST, 3) + TB> xo;
+  ao.init(obase, x, (ht << kTB) | w);
+  constexpr int p0 = LY::regrow(LAST, 0) < 0 ? -1 : LY::regrow(LAST, 0) + kTB;
+  constexpr int p1 = LY::regrow(LAST, 1) < 0 ? -1 : LY::regrow(LAST, 1) + kTB;
+  constexpr int p2 = LY::regrow(LAST, 2) < 0 ? -1 : LY::regrow(LAST, 2) + kTB;
+  constexpr int p3 = LY::regrow(LAST, 3) < 0 ? -1 : LY::regrow(LAST, 3) + kTB;
+  BitSum<p0, p1, p2, p3> xo;
   xo.init(x);
-  const uint32_t ko = (uint32_t)__popc(x & ((ht << TB) | w));
+  const uint32_t ko = (uint32_t)__popc(x & ((ht << kTB) | w));
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    AR::store_hint(out, ao.at((LY::reg_u(LAST, j) >> K) << TB), v[j], cv, ko + xo.at(j), pol_out);
+    AR::store_hint(out, ao.at((LY::reg_u(LAST, j) >> K) << kTB), v[j], cv, ko + xo.at(j), pol_out);
 }
 
-template <int UB>
-struct TiledShape {
-  static constexpr int kThreads = 1 << (UB - 4);
-  static constexpr int kMinBlocks = UB == 12 ? 2 : 1;
-  static constexpr size_t kSmem = (size_t)16 << UB;
-};
-
-template <int UB, int N, class AR>
-__global__ void __launch_bounds__(TiledShape<UB>::kThreads, TiledShape<UB>::kMinBlocks)
-    tiled_kernel(const void* __restrict__ G, void* __restrict__ out, int count, TiledCtrl* ws) {
-  constexpr int TB = UB - kCB;
-  extern __shared__ __align__(16) uint4 xbuf[];
-  __shared__ uint32_t smax[64];
-  __shared__ uint32_t sexp[AR::kScaled ? (8 << (N - TB)) : 1];
-  __shared__ int s_item;
+// ---------------------------------------------------------------------- consumers --
+template <int N, int RB, class AR, int CT>
+__device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Shared& sh, char* bufs, uint32_t buf0) {
+  using GE = Geo<N>;
+  using SY = NamedSync<1, CT>;
   constexpr uint32_t D = 1u << N;
-  constexpr int nb = 1 << (N - kCB);  // class blocks per matrix
-  constexpr int n1 = 1 << (N - TB);   // stage-1 tiles per block
-  constexpr int n2 = 1 << (N - TB);   // stage-2 items per block (8 octets x w groups)
-  constexpr int group = n1 + n2;
+  constexpr int nb = 1 << (N - kCB);
+  const uint32_t t = threadIdx.x;
   const int blocks = nb * count;
-  const int n_items = (blocks + 1) * group;
-  const uint32_t xaddr = (uint32_t)__cvta_generic_to_shared(xbuf);
-  const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
-  for (;;) {
-    __syncthreads();  // s_item and shared buffers are free
-    if (threadIdx.x == 0) s_item = atomicAdd(&ws->counter, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= n_items) break;
-    const int g = item / group, j = item % group;
-    if (j < n1) {
-      if (g >= blocks) continue;
-      const int b = g, s = b % kTiledSlots, gen = b / kTiledSlots;
-      const unsigned long long gbase = (unsigned long long)(b / nb) * D * D;
-      // the tile one resident wave ahead, when that item is a stage-1 tile too
-      const int nx = item + (int)gridDim.x, gn = nx / group, jn = nx % group;
-      if (jn < n1 && gn < blocks)
-        stage1_prefetch<UB, N, AR>(G, (unsigned long long)(gn / nb) * D * D, (uint32_t)(gn % nb), (uint32_t)jn);
-      if (gen > 0) wait_for(&ws->s2_done[s], n2 * gen, &ws->status);
-      stage1<UB, N, AR>(G, gbase, (uint32_t)(b % nb), (uint32_t)j, slot_of(ws, N, TB, s), xaddr, smax, pol_stream,
-                        pol_keep);
-      signal(&ws->s1_done[s]);
+  const uint64_t pol_keep = policy_evict_last(), pol_first = policy_evict_first();
+  for (int use = 0;; ++use) {
+    const int buf = use % kBufs;
+    const uint32_t full = (uint32_t)__cvta_generic_to_shared(&sh.full[buf]);
+    const uint32_t parity = (use / kBufs) & 1;
+    // consumer 0 waits (bounded) and broadcasts, so that all consumers leave together
+    if (t == 0) sh.ok = wait_phase(full, parity, &ws->status);
+    SY::sync();
+    if (!sh.ok) break;
+    for (int i = 0; i < kPolls && !mbar_try_wait(full, parity); ++i) {  // completes at once: acquires the data
+    }
+    const int item = sh.item[buf];
+    if (item < 0) break;
+    Item<N> it;
+    it.decode(item, blocks);
+    const int s = it.b % kTiledSlots, gen = it.b / kTiledSlots;
+    const uint32_t addr = buf0 + (uint32_t)(buf * GE::kBuf);
+    if (it.s1) {
+      stage1<N, RB, AR, CT>(addr, slot_base(ws, GE::kSlot, s), ws, s, gen, (uint32_t)it.j, sh, (uint32_t)use + 1u,
+                            pol_keep);
     } else {
-      if (g == 0) continue;
-      const int b = g - 1, s = b % kTiledSlots, gen = b / kTiledSlots;
-      wait_for(&ws->s1_done[s], n1 * (gen + 1), &ws->status);
-      stage2<UB, N, AR>(out, (unsigned long long)(b / nb) * D * D, (uint32_t)(b % nb), (uint32_t)(j - n1),
-                        slot_of(ws, N, TB, s), xaddr, smax, sexp, &ws->s2_done[s], pol_stream, pol_stream);
+      if (t == 0) red_release_add(&ws->s2_done[s], 1);  // the slot's data is in shared memory now
+      stage2<N, RB, AR, CT>(addr, bufs + (size_t)buf * GE::kBuf, out, (unsigned long long)(it.b / nb) * D * D,
+                            (uint32_t)(it.b % nb), (uint32_t)it.j, pol_first);
+    }
+    SY::sync();  // every consumer is done with the buffer and has issued its stores
+    if (t == 0) {
+      if (it.s1) red_release_add(&ws->s1_done[s], 1);
+      sh.consumed = use + 1;
+      // the buffer was read and written through the generic proxy; the next copy writes it
+      // through the async one
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive((uint32_t)__cvta_generic_to_shared(&sh.empty[buf]));
     }
   }
 }
 
-template <int UB, int N, class AR>
+template <int RB>
+struct TiledShape {
+  static constexpr int kConsumers = 1 << (kUB - RB);
+  static constexpr int kThreads = kConsumers + 32;
+};
+
+template <int N, int RB, class AR>
+__global__ void __launch_bounds__(TiledShape<RB>::kThreads, 1)
+    tiled_kernel(const void* __restrict__ G, void* __restrict__ out, int count, TiledCtrl* ws) {
+  constexpr int CT = TiledShape<RB>::kConsumers;
+  extern __shared__ __align__(1024) char bufs[];
+  __shared__ Shared sh;
+  const uint32_t t = threadIdx.x;
+  const uint32_t buf0 = (uint32_t)__cvta_generic_to_shared(bufs);
+  if (t == 0) {
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init((uint32_t)__cvta_generic_to_shared(&sh.full[b]), 1);
+      mbar_init((uint32_t)__cvta_generic_to_shared(&sh.empty[b]), 1);
+    }
+    sh.abort = 0;
+    sh.consumed = 0;
+    sh.issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (t < 64) sh.smax[t] = 0;
+  __syncthreads();
+  if (t >= (uint32_t)CT) {
+    producer<N, AR>(G, count, ws, sh, buf0);
+  } else {
+    consumer<N, RB, AR, CT>(out, count, ws, sh, bufs, buf0);
+  }
+  __syncthreads();
+  // after a wait gave up: wait (bounded) for copies still landing in buffers nobody consumed
+  if (t == (uint32_t)CT && sh.issued > sh.consumed) {
+    for (int use = sh.consumed; use < sh.issued; ++use) {
+      const uint32_t full = (uint32_t)__cvta_generic_to_shared(&sh.full[use % kBufs]);
+      for (int i = 0; i < kPolls && !mbar_try_wait(full, (use / kBufs) & 1); ++i) {
+      }
+    }
+  }
+}
+
+template <int N, int RB, class AR>
 cudaError_t launch_tiled_t(const void* G, int count, void* out, cudaStream_t st) {
-  constexpr int TB = UB - kCB;
-  const size_t bytes = kTiledCtrlBytes + (size_t)kTiledSlots * slot_bytes(N, TB);
+  using GE = Geo<N>;
   void* ws = nullptr;
-  cudaError_t e = tiled_workspace(st, bytes, &ws);
+  cudaError_t e = tiled_workspace(st, GE::kWorkspace, &ws);
   if (e != cudaSuccess) return e;
-  auto kern = tiled_kernel<UB, N, AR>;
-  static int grid = 0;  // one wave of resident CTAs
+  auto kern = tiled_kernel<N, RB, AR>;
+  constexpr size_t smem = kBufs * GE::kBuf;
+  static int grid = 0;  // one CTA per SM
   if (!grid) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TiledShape<UB>::kSmem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TiledShape<UB>::kThreads, TiledShape<UB>::kSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TiledShape<RB>::kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    grid = sms * per_sm;
+    grid = sms;
   }
-  // clear the counters (not the status word, which the host reads and clears)
-  e = cudaMemsetAsync(ws, 0, offsetof(TiledCtrl, status), st);
+  // clear the counters and class maxima, not the status word
+  e = cudaMemsetAsync(reinterpret_cast<char*>(ws) + offsetof(TiledCtrl, counter), 0,
+                      sizeof(TiledCtrl) - offsetof(TiledCtrl, counter), st);
   if (e != cudaSuccess) return e;
-  kern<<<grid, TiledShape<UB>::kThreads, TiledShape<UB>::kSmem, st>>>(G, out, count, reinterpret_cast<TiledCtrl*>(ws));
+  kern<<<grid, TiledShape<RB>::kThreads, smem, st>>>(G, out, count, reinterpret_cast<TiledCtrl*>(ws));
   return cudaGetLastError();
 }
 
-template <int UB, class AR>
+template <int RB, class AR>
 cudaError_t launch_tiled_n(const void* G, int N, int count, void* out, cudaStream_t st) {
   switch (N) {
-    case 12: return launch_tiled_t<UB, 12, AR>(G, count, out, st);
-    case 13: return launch_tiled_t<UB, 13, AR>(G, count, out, st);
-    case 14: return launch_tiled_t<UB, 14, AR>(G, count, out, st);
+    case 12: return launch_tiled_t<12, RB, AR>(G, count, out, st);
+    case 13: return launch_tiled_t<13, RB, AR>(G, count, out, st);
+    case 14: return launch_tiled_t<14, RB, AR>(G, count, out, st);
     default: return cudaErrorNotSupported;
   }
 }

@@ -45,7 +45,7 @@ namespace {
 bool variant_has(int variant, int N, bool compose) {
   if (variant == kVariantUnit13 || variant == kVariantUnit13x8) return N >= 7 && N <= 15;
   if (variant == kVariantUnit12 || variant == kVariantUnit12x8) return N >= 6 && N <= 14;
-  if (variant == kVariantTiled13 || variant == kVariantTiled12) return !compose && tiled_supported(N);
+  if (variant == kVariantTiled8 || variant == kVariantTiled16) return !compose && tiled_supported(N);
   return false;
 }
 
@@ -77,13 +77,16 @@ cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, boo
                            cudaStream_t s, int variant) {
   if (!variant) {
     variant = xordiag_get_variant(N, c64, compose);
-    if ((variant == kVariantTiled13 || variant == kVariantTiled12) && count > kTiledMaxCount)
+    if ((variant == kVariantTiled8 || variant == kVariantTiled16) &&
+        (count > kTiledMaxCount || (reinterpret_cast<uintptr_t>(in) & 15u)))
       variant = default_variant(N);
   }
   if (!variant_has(variant, N, compose)) return cudaErrorNotSupported;
-  if (variant == kVariantTiled13 || variant == kVariantTiled12) {
-    if (count > kTiledMaxCount) return cudaErrorNotSupported;
-    return launch_tiled(in, N, (int)count, c64, out, variant == kVariantTiled13 ? 13 : 12, s);
+  if (variant == kVariantTiled8 || variant == kVariantTiled16) {
+    // the bulk copies need 16-byte aligned sources: other G take the single-pass kernel
+    if (count > kTiledMaxCount || (reinterpret_cast<uintptr_t>(in) & 15u))
+      return launch_xordiag(in, N, count, c64, compose, scale_exp, out, s, default_variant(N));
+    return launch_tiled(in, N, (int)count, c64, out, variant == kVariantTiled8 ? 3 : 4, s);
   }
   if (c64)
     return compose ? xordiag_c64_compose(variant, N, in, count, scale_exp, out, s)

@@ -347,18 +347,28 @@ __device__ __forceinline__ void wht_regs(typename AR::Elem (&v)[E]) {
       if (!((j >> b) & 1)) AR::bfly(v[j], v[j | (1 << b)]);
 }
 
+// Barrier over the threads that hold a unit: the whole CTA, or (NamedSync) the first
+// THREADS threads on hardware barrier ID (warp-specialised kernels).
+struct CtaSync {
+  __device__ static __forceinline__ void sync() { __syncthreads(); }
+};
+template <int ID, int THREADS>
+struct NamedSync {
+  __device__ static __forceinline__ void sync() { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(THREADS) : "memory"); }
+};
+
 // Re-distribute the unit between threads from phase P's layout to phase P+1's, through shared
 // memory: 16-byte slots, slot(u) = u ^ swz(u) (XOR-linear, so thread part and register part
 // combine with one XOR; the base address is added afterwards).
-template <class LY, class AR, int P>
+template <class LY, class AR, int P, class SY = CtaSync>
 __device__ __forceinline__ void exchange(typename AR::Elem (&v)[LY::E], uint32_t xaddr, uint32_t t) {
-  __syncthreads();
+  SY::sync();
   const uint32_t ut = LY::thread_u(P, t);
   const uint32_t ft = ut ^ swz_term(ut);
 #pragma unroll
   for (int j = 0; j < LY::E; ++j)
     sts128(xaddr + 16u * (ft ^ (LY::reg_u(P, j) ^ swz_term(LY::reg_u(P, j)))), AR::pack(v[j]));
-  __syncthreads();
+  SY::sync();
   const uint32_t un = LY::thread_u(P + 1, t);
   const uint32_t fn = un ^ swz_term(un);
 #pragma unroll
@@ -367,12 +377,12 @@ __device__ __forceinline__ void exchange(typename AR::Elem (&v)[LY::E], uint32_t
 }
 
 // All phases of the local transform: butterflies, exchange, butterflies, ...
-template <class LY, class AR, int P = 0>
+template <class LY, class AR, int P = 0, class SY = CtaSync>
 __device__ __forceinline__ void local_wht(typename AR::Elem (&v)[LY::E], uint32_t xaddr, uint32_t t) {
   wht_regs<AR, LY::gcount(P), LY::E>(v);
   if constexpr (P + 1 < LY::NPH) {
-    exchange<LY, AR, P>(v, xaddr, t);
-    local_wht<LY, AR, P + 1>(v, xaddr, t);
+    exchange<LY, AR, P, SY>(v, xaddr, t);
+    local_wht<LY, AR, P + 1, SY>(v, xaddr, t);
   }
 }
 

@@ -1,6 +1,6 @@
-"""GPU parity of the two-stage tiled decomposition (PAULI_VARIANT_TILED8192 / TILED4096).
+"""GPU parity of the two-stage tiled decomposition (PAULI_VARIANT_TILED8 / TILED16).
 
-Stage 1 transforms 64 XY-masks x 2^TB rows per tile with a per-(class, tile) fixed-point
+Stage 1 transforms 64 XY-masks x 64 rows per tile with a per-(class, tile) fixed-point
 scale, stage 2 re-scales the tiles of each class to the class maximum and finishes the
 transform. Checked against the oracle on sampled coefficients (random and special indices),
 bit for bit on integer-valued inputs (every partial sum is exact on both sides, including
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {torch.complex128: 1e-12, torch.complex64: 2e-6}
 NP = {torch.complex128: np.complex128, torch.complex64: np.complex64}
-TILED = ("tiled8192", "tiled4096")
+TILED = ("tiled8", "tiled16")
 
 
 def dev(a):
@@ -92,7 +92,7 @@ def test_tiled_nonfinite_entry_gives_nan_for_its_mask_only():
     N = 12
     G = workloads.gaussian_complex(N, 2500)
     G[700, 3001] = np.inf
-    got = run_tiled(dev(G), N, torch.complex128, "tiled8192")
+    got = run_tiled(dev(G), N, torch.complex128, "tiled8")
     n_all = np.arange(4 ** N, dtype=np.int64)
     even = np.zeros_like(n_all)
     odd = np.zeros_like(n_all)
@@ -111,7 +111,7 @@ def test_tiled_batch_and_repeated_launches(dtype):
     N = 12
     Gs = np.stack([workloads.gaussian_complex(N, 2600 + b) for b in range(3)]).astype(NP[dtype])
     Gd = dev(Gs)
-    pg.set_variant(N, dtype, "decompose", "tiled8192")
+    pg.set_variant(N, dtype, "decompose", "tiled8")
     try:
         outs = [host(pg.decompose(Gd, method="xordiag")) for _ in range(3)]
         pg.stream_status()
@@ -125,8 +125,23 @@ def test_tiled_batch_and_repeated_launches(dtype):
         assert_close(outs[0][b][idx.astype(np.int64)], oracle.decompose_at(ref, idx), np.max(np.abs(ref)), dtype)
 
 
+def test_tiled_c64_unaligned_matrix_takes_single_pass_path():
+    """A complex64 G that is 8- but not 16-byte aligned cannot feed the bulk copies; the call
+    still succeeds (single-pass kernel) and matches the oracle."""
+    N = 12
+    G = workloads.gaussian_complex(N, 2700).astype(np.complex64)
+    flat = torch.empty(4 ** N + 1, dtype=torch.complex64, device="cuda")
+    flat[1:] = torch.from_numpy(G.ravel()).cuda()
+    Gd = flat[1:].view(1 << N, 1 << N)
+    assert Gd.data_ptr() % 16 == 8
+    got = run_tiled(Gd, N, torch.complex64, "tiled8")
+    idx = workloads.sample_indices(N, 2701, k=256)
+    assert_close(got[idx.astype(np.int64)], oracle.decompose_at(G.astype(np.complex128), idx), np.max(np.abs(G)),
+                 torch.complex64)
+
+
 def test_tiled_variant_is_decompose_only():
     with pytest.raises(pg.PauliError, match="UNSUPPORTED"):
-        pg.set_variant(14, torch.complex128, "compose", "tiled8192")
+        pg.set_variant(14, torch.complex128, "compose", "tiled8")
     with pytest.raises(pg.PauliError, match="UNSUPPORTED"):
-        pg.set_variant(11, torch.complex128, "decompose", "tiled8192")
+        pg.set_variant(11, torch.complex128, "decompose", "tiled8")
