@@ -5,6 +5,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "tiled.h"
 
 namespace pauli {
@@ -57,6 +59,45 @@ cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out) {
   g_ws.push_back(Workspace{dev, st, p, bytes});
   *out = p;
   return cudaSuccess;
+}
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link to libcuda).
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+cudaError_t tiled_tensor_map(CUtensorMap* map, const void* G, int N, int count, int elem) {
+  EncodeTiled fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  // `count` stacked D x D matrices as one (count D) x (D elem / 8) array of 8-byte words;
+  // a box is 64 rows of 64 elements
+  const cuuint64_t D = 1ull << N;
+  const cuuint64_t dims[2] = {D * (cuuint64_t)elem / 8, D * (cuuint64_t)count};
+  const cuuint64_t strides[1] = {D * (cuuint64_t)elem};
+  const cuuint32_t box[2] = {64u * (cuuint32_t)elem / 8, 64u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(G), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 bool tiled_supported(int N) { return N >= 12 && N <= 14; }

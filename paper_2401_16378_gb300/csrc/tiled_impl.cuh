@@ -30,21 +30,27 @@
 // holds 64 x 2^N partials each (16 MiB at N = 14); it is written with an L2 evict-last policy
 // and stays in L2 while G and c stream through with evict-first.
 //
-// Launch: one persistent CTA per SM, warp-specialised. A producer warp takes work items from
-// a global counter in the order S1(block 0), S1(1), S2(0), S1(2), S2(1), ..., waits for the
-// item's dependencies (a stage-2 item needs the 2^L tiles of its block; a stage-1 item needs
-// the stage-2 items of the block that last used its slot to have copied their data out), and
-// fills a 3-deep ring of shared-memory buffers with cp.async.bulk copies (64 row runs of 1 KiB
-// for a tile of complex128 G, one chunk for a stage-2 item) that complete on an mbarrier. The
-// consumer warps (512 threads x 8 elements or 256 x 16) take the buffers in order, compute,
-// store, publish completion with a release reduction and hand the buffer back. Loads for the
-// next two items are thus in flight while one is computed.
+// Launch: one persistent CTA per SM, warp-specialised.
+//  - a producer warp takes work items from a global counter in the order S1(block 0), S1(1),
+//    S2(0), S1(2), S2(1), ..., waits for the item's dependencies (a stage-2 item needs the 2^L
+//    tiles of its block; a stage-1 item needs the stage-2 items of the block that last used its
+//    slot to have copied their data out), and fills a 3-deep ring of shared-memory buffers: one
+//    2D TMA tensor load per stage-1 tile (64 rows of 64 elements), one bulk copy per stage-2
+//    chunk, completing on the buffer's mbarrier;
+//  - the consumer warps (512 threads x 8 elements or 256 x 16) take the buffers in order,
+//    compute and store; each warp hands the buffer back (mbarrier) as soon as it is done with it;
+//  - a release warp publishes each finished stage-1 tile to the other SMs (a release reduction
+//    on the slot's counter, which waits for the tile's stores to reach L2) off the consumers'
+//    critical path.
+// Loads for the next two items are in flight while one is computed.
 //
 // Every item waited on was taken from the counter earlier by a CTA that processes its items in
 // the order it took them, so every wait ends. Each wait is bounded nevertheless: after
 // kPolls polls the waiting thread records PAULI_ERR_TIMEOUT in the status word, the CTA stops
 // taking work, waits (bounded) for its copies in flight and exits; the results are then invalid.
 #pragma once
+#include <cuda.h>
+
 #include <cstddef>
 
 #include "kernels.h"
@@ -55,6 +61,9 @@ namespace pauli {
 
 // Scratch of at least `bytes` for launches on `st` (tiled.cu).
 cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out);
+// 2D tensor map of `count` stacked D x D matrices with `elem` bytes per element, box of
+// 64 rows x 64 elements (tiled.cu).
+cudaError_t tiled_tensor_map(CUtensorMap* map, const void* G, int N, int count, int elem);
 
 namespace tiled {
 namespace {
@@ -69,16 +78,16 @@ constexpr int kStatusTimeout = 8;  // PAULI_ERR_TIMEOUT
 
 template <int N>
 struct Geo {
-  static constexpr int L = N - kTB;        // stage-2 bits (row blocks)
-  static constexpr int K2 = kUB - L;       // stage-2 class bits: 3 (octet) + ZB (w)
+  static constexpr int L = N - kTB;           // stage-2 bits (row blocks)
+  static constexpr int K2 = kUB - L;          // stage-2 class bits: 3 (octet) + ZB (w)
   static constexpr int ZB = K2 - 3;
-  static constexpr int NR = 1 << L;        // tiles per block
+  static constexpr int NR = 1 << L;           // tiles per block
   static constexpr int NQ = 1 << (kTB - ZB);  // w groups per octet
-  static constexpr int n1 = NR;            // stage-1 items per block
-  static constexpr int n2 = 8 * NQ;        // stage-2 items per block
-  static constexpr size_t kChunk = (size_t)16 << kUB;          // bytes per item (64 KiB)
-  static constexpr size_t kEOct = (size_t)NR * 8 * 4;          // E bytes per octet
-  static constexpr size_t kBuf = kChunk + kEOct + 128;         // buffer: data, E, class maxima
+  static constexpr int n1 = NR;               // stage-1 items per block
+  static constexpr int n2 = 8 * NQ;           // stage-2 items per block
+  static constexpr size_t kChunk = (size_t)16 << kUB;   // bytes per item (64 KiB)
+  static constexpr size_t kEOct = (size_t)NR * 8 * 4;   // E bytes per octet
+  static constexpr size_t kBuf = kChunk + kEOct + 128;  // buffer: data, E, class maxima
   static constexpr size_t kSlotP = (size_t)16 << (N + kCB);
   static constexpr size_t kSlot = kSlotP + (size_t)NR * 64 * 4;
   static constexpr size_t kWorkspace = kTiledCtrlBytes + kTiledSlots * kSlot;
@@ -109,6 +118,9 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 }
 __device__ __forceinline__ void red_release_add(int* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_relaxed_add(int* p, int v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void red_max(uint32_t* p, uint32_t v) {
   asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -141,16 +153,27 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(bar), "l"(pol)
       : "memory");
 }
+// 2D tensor tile (x = innermost coordinate, in the map's 8-byte elements; y = row)
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared state of one CTA.
 struct Shared {
-  uint64_t full[kBufs];   // buffer filled (producer arrival + copied bytes)
-  uint64_t empty[kBufs];  // buffer released by the consumers
+  uint64_t full[kBufs];   // buffer filled: producer arrival + copied bytes
+  uint64_t empty[kBufs];  // buffer released: one arrival per consumer warp
+  uint64_t done[kBufs];   // item's stores issued: one arrival per consumer warp (release warp waits)
   int item[kBufs];        // work item in the buffer, -1 = no more work
-  int abort;              // a wait of the producer gave up: stop
+  int rel_slot[kBufs];    // per buffer use: slot to publish (stage 1), -1 (stage 2), -2 (end)
   int ok;                 // consumers: the next buffer arrived (broadcast by consumer 0)
-  int consumed;           // buffer uses completed by the consumers
+  int waited;             // buffer uses whose data consumer 0 has waited for
   int issued;             // buffer uses whose copies the producer has issued
+  int released;           // buffer uses the release warp has handled
   uint32_t smax[64];      // stage 1: (use + 1) << 11 | largest exponent of each class
 };
 
@@ -193,43 +216,34 @@ __device__ __forceinline__ char* slot_base(TiledCtrl* ws, size_t slot_bytes, int
 
 // ---------------------------------------------------------------------- producer --
 template <int N, class AR>
-__device__ void producer(const void* __restrict__ G, int count, TiledCtrl* ws, Shared& sh, uint32_t buf0) {
+__device__ void producer(const CUtensorMap* map, int count, TiledCtrl* ws, Shared& sh, uint32_t buf0) {
   using GE = Geo<N>;
   constexpr uint32_t D = 1u << N;
   constexpr int nb = 1 << (N - kCB);
-  constexpr uint32_t kRowBytes = 64u * sizeof(typename AR::Raw);
+  constexpr uint32_t kTileBytes = 64u * 64u * sizeof(typename AR::Raw);
+  constexpr int kX = (int)sizeof(typename AR::Raw) / 8;  // map elements per matrix element
   const int lane = threadIdx.x & 31;
   const int blocks = nb * count;
   const int n_items = (blocks + 1) * (GE::n1 + GE::n2);
   const uint64_t pol_first = policy_evict_first();
-  int next = 0;
-  if (lane == 0) next = atomicAdd(&ws->counter, 1);
-  next = __shfl_sync(0xFFFFFFFFu, next, 0);
-  int use = 0;
-  for (;;) {
+  if (lane != 0) return;  // one thread drives the ring
+  asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+  int next = atomicAdd(&ws->counter, 1);
+  for (int use = 0;;) {
     const int item = next;
     const bool done = item >= n_items;
     Item<N> it;
-    bool real = false;
     if (!done) {
-      if (lane == 0) next = atomicAdd(&ws->counter, 1);  // latency overlaps the rest of this item
-      next = __shfl_sync(0xFFFFFFFFu, next, 0);
-      real = it.decode(item, blocks);
-      if (!real) continue;
+      next = atomicAdd(&ws->counter, 1);  // its latency overlaps the rest of this item
+      if (!it.decode(item, blocks)) continue;
     }
     const int buf = use % kBufs;
-    const uint32_t full = (uint32_t)__cvta_generic_to_shared(&sh.full[buf]);
-    const uint32_t empty = (uint32_t)__cvta_generic_to_shared(&sh.empty[buf]);
+    const uint32_t full = smem_addr(&sh.full[buf]);
+    if (use >= kBufs && !wait_phase(smem_addr(&sh.empty[buf]), ((use / kBufs) - 1) & 1, &ws->status))
+      break;  // the consumers never released the buffer: they give up on their own wait
     bool ok = true;
-    if (lane == 0 && use >= kBufs) ok = wait_phase(empty, ((use / kBufs) - 1) & 1, &ws->status);
-    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-    if (!ok) {  // the consumers never released the buffer: they time out on their own wait
-      if (lane == 0) sh.abort = 1;
-      break;
-    }
     const int s = done ? 0 : it.b % kTiledSlots, gen = done ? 0 : it.b / kTiledSlots;
-    if (lane == 0 && !done) {
-      // dependencies: the slot must be free (stage 1) or complete (stage 2)
+    if (!done) {  // dependencies: the slot must be free (stage 1) or complete (stage 2)
       if (it.s1) {
         if (gen > 0) ok = wait_count(&ws->s2_done[s], GE::n2 * gen, &ws->status);
       } else {
@@ -238,31 +252,20 @@ __device__ void producer(const void* __restrict__ G, int count, TiledCtrl* ws, S
         asm volatile("fence.proxy.async.global;" ::: "memory");
       }
     }
-    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
     if (done || !ok) {  // no more work (or a dependency never came): tell the consumers
-      if (lane == 0) {
-        if (!ok) sh.abort = 1;
-        sh.item[buf] = -1;
-        mbar_arrive(full);
-      }
+      sh.item[buf] = -1;
+      mbar_arrive(full);
       break;
     }
     const uint32_t dst = buf0 + (uint32_t)(buf * GE::kBuf);
-    if (lane == 0) {
-      sh.item[buf] = item;
-      const uint32_t bytes = it.s1 ? kRowBytes * 64u : (uint32_t)(GE::kChunk + GE::kEOct + 32);
-      mbar_arrive_tx(full, bytes);
-    }
-    __syncwarp();
+    sh.item[buf] = item;
     if (it.s1) {
-      const uint32_t k = (uint32_t)(it.b % nb), R = (uint32_t)it.j;
-      const uint32_t row0 = R << kTB, colb = (row0 ^ (k << kCB)) & ~63u;
-      const char* base = reinterpret_cast<const char*>(G) +
-                         (size_t)(it.b / nb) * D * D * sizeof(typename AR::Raw);
-      for (int r = lane; r < 64; r += 32)
-        bulk_g2s(dst + (uint32_t)r * kRowBytes,
-                 base + ((size_t)(row0 + r) * D + colb) * sizeof(typename AR::Raw), kRowBytes, full, pol_first);
-    } else if (lane == 0) {
+      mbar_arrive_tx(full, kTileBytes);
+      const uint32_t k = (uint32_t)(it.b % nb), row0 = (uint32_t)it.j << kTB;
+      const uint32_t colb = (row0 ^ (k << kCB)) & ~63u;
+      tma_2d(dst, map, (int)colb * kX, (int)((uint32_t)(it.b / nb) * D + row0), full, pol_first);
+    } else {
+      mbar_arrive_tx(full, (uint32_t)(GE::kChunk + GE::kEOct + 32));
       const uint32_t o = (uint32_t)it.j & 7u, q = (uint32_t)it.j >> 3;
       char* sb = slot_base(ws, GE::kSlot, s);
       bulk_g2s(dst, sb + (size_t)(o * GE::NQ + q) * GE::kChunk, (uint32_t)GE::kChunk, full, pol_first);
@@ -271,30 +274,79 @@ __device__ void producer(const void* __restrict__ G, int count, TiledCtrl* ws, S
       bulk_g2s(dst + (uint32_t)(GE::kChunk + GE::kEOct), &ws->emax[s][o * 8], 32u, full, pol_first);
     }
     ++use;
-    if (lane == 0) sh.issued = use;
+    sh.issued = use;
+  }
+}
+
+// ------------------------------------------------------------------- release warp --
+// Publishes finished stage-1 tiles, in the consumers' order (one thread).
+__device__ void releaser(TiledCtrl* ws, Shared& sh) {
+  if ((threadIdx.x & 31) != 0) return;
+  volatile int* released = &sh.released;
+  for (int use = 0;; ++use) {
+    const int buf = use % kBufs;
+    if (!wait_phase(smem_addr(&sh.done[buf]), (use / kBufs) & 1, &ws->status)) break;
+    const int r = sh.rel_slot[buf];
+    if (r == -2) break;
+    // every consumer warp's stores precede its arrival; the release makes them visible first
+    if (r >= 0) red_release_add(&ws->s1_done[r], 1);
+    *released = use + 1;
   }
 }
 
 // ---------------------------------------------------------------------- stage 1 --
-// Tile R of block k from the buffer: element (i, c) at 16-byte slot (i << 6) | (i ^ c).
+// Per-thread constants of the stage-1 layout (computed once per thread).
+template <int RB, int N>
+struct S1Thread {
+  using LY = Layout<kUB, kTB, RB>;
+  uint32_t c;       // class within the block
+  uint32_t ld;      // 16-byte slot of the thread's register-0 element in the tile: (i << 6) | (i ^ c)
+  uint32_t xw, xr;  // swizzled exchange slots (write at phase 0, read at phase 1)
+  uint32_t st;      // scratch entry of the thread's register-0 output, without the tile offset
+  __device__ __forceinline__ void init(uint32_t t) {
+    using GE = Geo<N>;
+    constexpr int LAST = LY::NPH - 1;
+    static_assert(LY::NPH == 2, "one exchange");
+    c = t & 63u;
+    const uint32_t it = LY::thread_u(0, t) >> kCB;
+    ld = (it << 6) | (it ^ c);
+    const uint32_t u0 = LY::thread_u(0, t), u1 = LY::thread_u(1, t);
+    xw = u0 ^ swz_term(u0);
+    xr = u1 ^ swz_term(u1);
+    const uint32_t wt = LY::thread_u(LAST, t) >> kCB;
+    st = (c >> 3) * GE::NQ * (uint32_t)(GE::kChunk / 16) + (c & 7u) + (wt >> GE::ZB) * (uint32_t)(GE::kChunk / 16) +
+         ((wt & ((1u << GE::ZB) - 1u)) << 3);
+  }
+};
+
+// Register j's offset from the thread's register-0 entry (compile-time).
+template <class LY, int N>
+__host__ __device__ constexpr uint32_t s1_store_off(int j) {
+  using GE = Geo<N>;
+  const uint32_t w = LY::reg_u(LY::NPH - 1, j) >> kCB;
+  return (w >> GE::ZB) * (uint32_t)(GE::kChunk / 16) + ((w & ((1u << GE::ZB) - 1u)) << 3);
+}
+template <class LY>
+__host__ __device__ constexpr uint32_t s1_load_off(int j) {
+  const uint32_t i = LY::reg_u(0, j) >> kCB;
+  return (i << 6) | i;  // XORed into the thread's slot (the bits are the thread's zero bits)
+}
+
+// Tile R of block k in the buffer: element (i, c) at slot (i << 6) | (i ^ c).
 template <int N, int RB, class AR, int CT>
-__device__ __forceinline__ void stage1(uint32_t tile, char* slot, TiledCtrl* ws, int s, int gen, uint32_t R,
-                                       Shared& sh, uint32_t tag, uint64_t pol_keep) {
+__device__ __forceinline__ void stage1(uint32_t tile, const S1Thread<RB, N>& th, char* slot, TiledCtrl* ws, int s,
+                                       int gen, uint32_t R, Shared& sh, uint32_t tag, uint64_t pol_keep) {
   using GE = Geo<N>;
   using LY = Layout<kUB, kTB, RB>;
   using SY = NamedSync<1, CT>;
   static_assert(LY::K == kCB, "tile = 64 classes x 64 rows");
-  constexpr int E = LY::E, LAST = LY::NPH - 1;
+  constexpr int E = LY::E;
   constexpr uint32_t kEs = sizeof(typename AR::Raw);
-  const uint32_t t = threadIdx.x;
-  const uint32_t c = t & 63u;
-  const uint32_t it = LY::thread_u(0, t) >> kCB;
   typename AR::Raw raw[E];
   uint32_t emax = 0;
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const uint32_t i = it | (LY::reg_u(0, j) >> kCB);
-    const uint32_t a = tile + ((i << 6) | (i ^ c)) * kEs;
+    const uint32_t a = tile + (th.ld ^ s1_load_off<LY>(j)) * kEs;
     if constexpr (kEs == 16) {
       raw[j] = AR::raw_unpack(lds128(a));
     } else {
@@ -306,83 +358,121 @@ __device__ __forceinline__ void stage1(uint32_t tile, char* slot, TiledCtrl* ws,
   }
   uint32_t Ekey = 0;
   if constexpr (AR::kScaled) {
-    atomicMax(&sh.smax[c], (tag << 11) | (emax >> 20));  // older tags are smaller: no reset needed
-    SY::sync();
-    Ekey = (sh.smax[c] & 0x7FFu) << 20;
+    atomicMax(&sh.smax[th.c], (tag << 11) | (emax >> 20));  // older tags are smaller: no reset needed
   }
+  SY::sync();  // exponents complete, and every tile read is done: the buffer serves the exchange
+  if constexpr (AR::kScaled) Ekey = (sh.smax[th.c] & 0x7FFu) << 20;
   const typename AR::Conv cv = AR::make_conv(N, Ekey, 0);
   typename AR::Elem v[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) v[j] = AR::template convert<0>(raw[j], cv, 0u);
-  local_wht<LY, AR, 0, SY>(v, tile, t);  // the first exchange barrier also ends the tile reads
-  // P[o][q][R][wl][c8]: o = c >> 3, c8 = c & 7, w = (q << ZB) | wl
-  const uint32_t wt = LY::thread_u(LAST, t) >> kCB;
-  uint4* P = reinterpret_cast<uint4*>(slot);
-  const size_t cbase = (size_t)(c >> 3) * GE::NQ * (GE::kChunk / 16) + (c & 7u);
+  wht_regs<AR, LY::gcount(0), E>(v);
+  // exchange phase 0 -> 1 (the barrier above already ended the reads of the tile)
 #pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const uint32_t w = wt | (LY::reg_u(LAST, j) >> kCB);
-    const uint32_t q = w >> GE::ZB, wl = w & ((1u << GE::ZB) - 1u);
-    st_hint(P + cbase + (size_t)q * (GE::kChunk / 16) + (((R << GE::ZB) | wl) << 3), AR::pack(v[j]), pol_keep);
-  }
-  if (t < 64) {
+  for (int j = 0; j < E; ++j)
+    sts128(tile + 16u * (th.xw ^ (LY::reg_u(0, j) ^ swz_term(LY::reg_u(0, j)))), AR::pack(v[j]));
+  SY::sync();
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    v[j] = AR::unpack(lds128(tile + 16u * (th.xr ^ (LY::reg_u(1, j) ^ swz_term(LY::reg_u(1, j))))));
+  wht_regs<AR, LY::gcount(1), E>(v);
+  // P[o][q][R][wl][c8]
+  uint4* P = reinterpret_cast<uint4*>(slot) + th.st + (R << (GE::ZB + 3));
+#pragma unroll
+  for (int j = 0; j < E; ++j) st_hint(P + s1_store_off<LY, N>(j), AR::pack(v[j]), pol_keep);
+  if (threadIdx.x < 64) {
     uint32_t* Ep = reinterpret_cast<uint32_t*>(slot + GE::kSlotP);
-    Ep[((t >> 3) * GE::NR + R) * 8 + (t & 7u)] = Ekey;
-    if constexpr (AR::kScaled) red_max(&ws->emax[s][t], ((uint32_t)(gen + 1) << 11) | (Ekey >> 20));
+    Ep[((threadIdx.x >> 3) * GE::NR + R) * 8 + (threadIdx.x & 7u)] = Ekey;
+    if constexpr (AR::kScaled) red_max(&ws->emax[s][threadIdx.x], ((uint32_t)(gen + 1) << 11) | (Ekey >> 20));
   }
 }
 
 // ---------------------------------------------------------------------- stage 2 --
+template <int RB, int N>
+struct S2Thread {
+  using LY = Layout<kUB, Geo<N>::L, RB>;
+  static constexpr int NPH = LY::NPH;
+  uint32_t c8, wt;     // class within the octet, thread part of w (without the item's group)
+  uint32_t u0;         // thread part of the element index at phase 0
+  uint32_t ex[2 * (NPH - 1)];  // swizzled exchange slots: write/read per exchange
+  uint32_t ht;         // thread part of h at the last phase
+  __device__ __forceinline__ void init(uint32_t t) {
+    constexpr int ZB = Geo<N>::ZB;
+    c8 = t & 7u;
+    wt = (t >> 3) & ((1u << ZB) - 1u);
+    u0 = LY::thread_u(0, t);
+#pragma unroll
+    for (int p = 0; p + 1 < NPH; ++p) {
+      const uint32_t a = LY::thread_u(p, t), b = LY::thread_u(p + 1, t);
+      ex[2 * p] = a ^ swz_term(a);
+      ex[2 * p + 1] = b ^ swz_term(b);
+    }
+    ht = LY::thread_u(NPH - 1, t) >> LY::K;
+  }
+};
+
+template <class LY, class AR, class SY, int P>
+__device__ __forceinline__ void s2_phases(typename AR::Elem (&v)[LY::E], uint32_t xaddr, const uint32_t* ex) {
+  wht_regs<AR, LY::gcount(P), LY::E>(v);
+  if constexpr (P + 1 < LY::NPH) {
+    SY::sync();  // previous reads of the buffer are done
+#pragma unroll
+    for (int j = 0; j < LY::E; ++j)
+      sts128(xaddr + 16u * (ex[2 * P] ^ (LY::reg_u(P, j) ^ swz_term(LY::reg_u(P, j)))), AR::pack(v[j]));
+    SY::sync();
+#pragma unroll
+    for (int j = 0; j < LY::E; ++j)
+      v[j] = AR::unpack(lds128(xaddr + 16u * (ex[2 * P + 1] ^ (LY::reg_u(P + 1, j) ^ swz_term(LY::reg_u(P + 1, j))))));
+    s2_phases<LY, AR, SY, P + 1>(v, xaddr, ex);
+  }
+}
+
 // Item j = (o, q) of block k: the chunk holds entry (R, wl, c8) at 16-byte slot
 // (R << K2) | (wl << 3) | c8 -- the unit's own element order -- then E[R][c8], then the
 // eight tagged class maxima.
 template <int N, int RB, class AR, int CT>
-__device__ __forceinline__ void stage2(uint32_t chunk, const char* chunk_gen, void* __restrict__ out,
-                                       unsigned long long obase, uint32_t k, uint32_t item, uint64_t pol_out) {
+__device__ __forceinline__ void stage2(uint32_t chunk, const char* chunk_gen, const S2Thread<RB, N>& th,
+                                       void* __restrict__ out, unsigned long long obase, uint32_t k, uint32_t item,
+                                       uint64_t pol_out) {
   using GE = Geo<N>;
   using LY = Layout<kUB, GE::L, RB>;
   using SY = NamedSync<1, CT>;
   constexpr int K = LY::K, E = LY::E, LAST = LY::NPH - 1, ZB = GE::ZB;
   static_assert(K == GE::K2, "stage-2 unit = 8 classes x 2^ZB w x 2^L row blocks");
-  const uint32_t t = threadIdx.x;
   const uint32_t o = item & 7u, q = item >> 3;
-  const uint32_t c8 = t & 7u;
-  const uint32_t w = (q << ZB) | ((t >> 3) & ((1u << ZB) - 1u));
-  const uint32_t x = (k << kCB) | (o << 3) | c8;
-  const uint32_t u0 = LY::thread_u(0, t);
+  const uint32_t w = (q << ZB) | th.wt;
+  const uint32_t x = (k << kCB) | (o << 3) | th.c8;
   typename AR::Elem v[E];
 #pragma unroll
-  for (int j = 0; j < E; ++j) v[j] = AR::unpack(lds128(chunk + 16u * (u0 | LY::reg_u(0, j))));
+  for (int j = 0; j < E; ++j) v[j] = AR::unpack(lds128(chunk + 16u * (th.u0 + LY::reg_u(0, j))));
   typename AR::Conv cv;
   if constexpr (AR::kScaled) {
     const uint32_t* Es = reinterpret_cast<const uint32_t*>(chunk_gen + GE::kChunk);
-    const int em = (int)(Es[GE::NR * 8 + c8] & 0x7FFu);
+    const int em = (int)(Es[GE::NR * 8 + th.c8] & 0x7FFu);
     cv = AR::make_conv(N, (uint32_t)em << 20, -N);
     if (!cv.nan) {
-      const uint32_t Rt = u0 >> K;
+      const uint32_t* Et = Es + (((th.u0 >> K) << 3) | th.c8);
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const uint32_t Rb = Rt | (LY::reg_u(0, j) >> K);
         // tile at exponent et was converted at scale 2^(s + em - et): shift right by em - et
         // (all-zero tiles have et = 0 and hold zeros)
-        AR::align(v[j], min(em - (int)(Es[(Rb << 3) | c8] >> 20), 63));
+        AR::align(v[j], min(em - (int)(Et[(LY::reg_u(0, j) >> K) << 3] >> 20), 63));
       }
     }
   } else {
     cv = AR::make_conv(N, 0u, -N);
   }
-  local_wht<LY, AR, 0, SY>(v, chunk, t);  // the first exchange barrier also ends the chunk reads
+  s2_phases<LY, AR, SY, 0>(v, chunk, th.ex);  // the first barrier also ends the chunk reads
   // c(x, z), z = (h << 6) | w, h = ht | (register part)
-  const uint32_t ht = LY::thread_u(LAST, t) >> K;
   Addr<N, false> ao;
-  ao.init(obase, x, (ht << kTB) | w);
+  ao.init(obase, x, (th.ht << kTB) | w);
   constexpr int p0 = LY::regrow(LAST, 0) < 0 ? -1 : LY::regrow(LAST, 0) + kTB;
   constexpr int p1 = LY::regrow(LAST, 1) < 0 ? -1 : LY::regrow(LAST, 1) + kTB;
   constexpr int p2 = LY::regrow(LAST, 2) < 0 ? -1 : LY::regrow(LAST, 2) + kTB;
   constexpr int p3 = LY::regrow(LAST, 3) < 0 ? -1 : LY::regrow(LAST, 3) + kTB;
   BitSum<p0, p1, p2, p3> xo;
   xo.init(x);
-  const uint32_t ko = (uint32_t)__popc(x & ((ht << kTB) | w));
+  const uint32_t ko = (uint32_t)__popc(x & ((th.ht << kTB) | w));
 #pragma unroll
   for (int j = 0; j < E; ++j)
     AR::store_hint(out, ao.at((LY::reg_u(LAST, j) >> K) << kTB), v[j], cv, ko + xo.at(j), pol_out);
@@ -395,15 +485,35 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
   using SY = NamedSync<1, CT>;
   constexpr uint32_t D = 1u << N;
   constexpr int nb = 1 << (N - kCB);
-  const uint32_t t = threadIdx.x;
+  const uint32_t t = threadIdx.x, lane = t & 31u;
   const int blocks = nb * count;
   const uint64_t pol_keep = policy_evict_last(), pol_first = policy_evict_first();
-  for (int use = 0;; ++use) {
+  S1Thread<RB, N> t1;
+  S2Thread<RB, N> t2;
+  t1.init(t);
+  t2.init(t);
+  volatile int* released = &sh.released;
+  int use = 0;
+  for (;; ++use) {
     const int buf = use % kBufs;
-    const uint32_t full = (uint32_t)__cvta_generic_to_shared(&sh.full[buf]);
+    const uint32_t full = smem_addr(&sh.full[buf]);
     const uint32_t parity = (use / kBufs) & 1;
-    // consumer 0 waits (bounded) and broadcasts, so that all consumers leave together
-    if (t == 0) sh.ok = wait_phase(full, parity, &ws->status);
+    // consumer 0 waits (bounded) and broadcasts, so that all consumers leave together; it also
+    // keeps the release warp less than a ring behind (its barrier phases must not be lapped)
+    if (t == 0) {
+      bool ok = true;
+      for (int i = 0; *released < use - kBufs + 1; ++i) {
+        if (i == kPolls) {
+          atomicExch(&ws->status, kStatusTimeout);
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+      ok = ok && wait_phase(full, parity, &ws->status);
+      if (ok) sh.waited = use + 1;
+      sh.ok = ok;
+    }
     SY::sync();
     if (!sh.ok) break;
     for (int i = 0; i < kPolls && !mbar_try_wait(full, parity); ++i) {  // completes at once: acquires the data
@@ -414,62 +524,75 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
     it.decode(item, blocks);
     const int s = it.b % kTiledSlots, gen = it.b / kTiledSlots;
     const uint32_t addr = buf0 + (uint32_t)(buf * GE::kBuf);
+    if (t == 0) sh.rel_slot[buf] = it.s1 ? s : -1;
     if (it.s1) {
-      stage1<N, RB, AR, CT>(addr, slot_base(ws, GE::kSlot, s), ws, s, gen, (uint32_t)it.j, sh, (uint32_t)use + 1u,
+      stage1<N, RB, AR, CT>(addr, t1, slot_base(ws, GE::kSlot, s), ws, s, gen, (uint32_t)it.j, sh, (uint32_t)use + 1u,
                             pol_keep);
     } else {
-      if (t == 0) red_release_add(&ws->s2_done[s], 1);  // the slot's data is in shared memory now
-      stage2<N, RB, AR, CT>(addr, bufs + (size_t)buf * GE::kBuf, out, (unsigned long long)(it.b / nb) * D * D,
+      // the slot's data is in shared memory: a relaxed count suffices (the copy has completed)
+      if (t == 0) red_relaxed_add(&ws->s2_done[s], 1);
+      stage2<N, RB, AR, CT>(addr, bufs + (size_t)buf * GE::kBuf, t2, out, (unsigned long long)(it.b / nb) * D * D,
                             (uint32_t)(it.b % nb), (uint32_t)it.j, pol_first);
     }
-    SY::sync();  // every consumer is done with the buffer and has issued its stores
-    if (t == 0) {
-      if (it.s1) red_release_add(&ws->s1_done[s], 1);
-      sh.consumed = use + 1;
-      // the buffer was read and written through the generic proxy; the next copy writes it
-      // through the async one
+    // this warp is done with the buffer and has issued its stores
+    __syncwarp();
+    if (lane == 0) {
+      // the buffer was accessed through the generic proxy; the next copy writes it through the async one
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive((uint32_t)__cvta_generic_to_shared(&sh.empty[buf]));
+      mbar_arrive(smem_addr(&sh.empty[buf]));
+      mbar_arrive(smem_addr(&sh.done[buf]));
     }
   }
+  // tell the release warp to stop: a last done phase marked -2 (after the previous uses'
+  // phases, which every warp has arrived on)
+  const int buf = use % kBufs;
+  if (t == 0) sh.rel_slot[buf] = -2;
+  SY::sync();
+  if (lane == 0) mbar_arrive(smem_addr(&sh.done[buf]));
 }
 
 template <int RB>
 struct TiledShape {
   static constexpr int kConsumers = 1 << (kUB - RB);
-  static constexpr int kThreads = kConsumers + 32;
+  static constexpr int kWarps = kConsumers / 32;
+  static constexpr int kThreads = kConsumers + 64;  // + producer warp + release warp
 };
 
 template <int N, int RB, class AR>
 __global__ void __launch_bounds__(TiledShape<RB>::kThreads, 1)
-    tiled_kernel(const void* __restrict__ G, void* __restrict__ out, int count, TiledCtrl* ws) {
+    tiled_kernel(const __grid_constant__ CUtensorMap map, void* __restrict__ out, int count, TiledCtrl* ws) {
   constexpr int CT = TiledShape<RB>::kConsumers;
   extern __shared__ __align__(1024) char bufs[];
   __shared__ Shared sh;
   const uint32_t t = threadIdx.x;
-  const uint32_t buf0 = (uint32_t)__cvta_generic_to_shared(bufs);
+  const uint32_t buf0 = smem_addr(bufs);
   if (t == 0) {
     for (int b = 0; b < kBufs; ++b) {
-      mbar_init((uint32_t)__cvta_generic_to_shared(&sh.full[b]), 1);
-      mbar_init((uint32_t)__cvta_generic_to_shared(&sh.empty[b]), 1);
+      mbar_init(smem_addr(&sh.full[b]), 1);
+      mbar_init(smem_addr(&sh.empty[b]), TiledShape<RB>::kWarps);
+      mbar_init(smem_addr(&sh.done[b]), TiledShape<RB>::kWarps);
     }
-    sh.abort = 0;
-    sh.consumed = 0;
+    sh.waited = 0;
     sh.issued = 0;
+    sh.released = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (t < 64) sh.smax[t] = 0;
   __syncthreads();
-  if (t >= (uint32_t)CT) {
-    producer<N, AR>(G, count, ws, sh, buf0);
-  } else {
+  if (t < (uint32_t)CT) {
     consumer<N, RB, AR, CT>(out, count, ws, sh, bufs, buf0);
+  } else if (t < (uint32_t)CT + 32) {
+    producer<N, AR>(&map, count, ws, sh, buf0);
+    __syncwarp();  // lane 0 drove the ring alone; the barrier below wants whole warps
+  } else {
+    releaser(ws, sh);
+    __syncwarp();
   }
   __syncthreads();
-  // after a wait gave up: wait (bounded) for copies still landing in buffers nobody consumed
-  if (t == (uint32_t)CT && sh.issued > sh.consumed) {
-    for (int use = sh.consumed; use < sh.issued; ++use) {
-      const uint32_t full = (uint32_t)__cvta_generic_to_shared(&sh.full[use % kBufs]);
+  // after a wait gave up: wait (bounded) for copies still landing in buffers nobody waited for
+  if (t == (uint32_t)CT && sh.issued > sh.waited) {
+    for (int use = sh.waited; use < sh.issued; ++use) {
+      const uint32_t full = smem_addr(&sh.full[use % kBufs]);
       for (int i = 0; i < kPolls && !mbar_try_wait(full, (use / kBufs) & 1); ++i) {
       }
     }
@@ -481,6 +604,9 @@ cudaError_t launch_tiled_t(const void* G, int count, void* out, cudaStream_t st)
   using GE = Geo<N>;
   void* ws = nullptr;
   cudaError_t e = tiled_workspace(st, GE::kWorkspace, &ws);
+  if (e != cudaSuccess) return e;
+  CUtensorMap map;
+  e = tiled_tensor_map(&map, G, N, count, (int)sizeof(typename AR::Raw));
   if (e != cudaSuccess) return e;
   auto kern = tiled_kernel<N, RB, AR>;
   constexpr size_t smem = kBufs * GE::kBuf;
@@ -500,7 +626,7 @@ cudaError_t launch_tiled_t(const void* G, int count, void* out, cudaStream_t st)
   e = cudaMemsetAsync(reinterpret_cast<char*>(ws) + offsetof(TiledCtrl, counter), 0,
                       sizeof(TiledCtrl) - offsetof(TiledCtrl, counter), st);
   if (e != cudaSuccess) return e;
-  kern<<<grid, TiledShape<RB>::kThreads, smem, st>>>(G, out, count, reinterpret_cast<TiledCtrl*>(ws));
+  kern<<<grid, TiledShape<RB>::kThreads, smem, st>>>(map, out, count, reinterpret_cast<TiledCtrl*>(ws));
   return cudaGetLastError();
 }
 
