@@ -119,8 +119,8 @@ struct FixConv {
   int rbase;      // right shift of the (pre-shifted) significand is rbase - exponent field
   int obias;      // biased FP64 exponent of 2^63 * output scale
   uint32_t oexp;  // (obias - 1 - 63 + 31 + 127 ... ) folded constant, see from_fixed
-  bool slow;      // tiny class maximum: zeros and underflow need the general path
-  bool nan;       // class contains Inf or NaN
+  bool slow;      // tiny class maximum (zeros and underflow need the general path), or NaN
+  bool nan;       // class contains Inf or NaN: every output is NaN
 };
 
 // round-toward-zero(v * 2^s) of the double (hi, lo) as int64; LPRE = max(0, 9 - N) is a
@@ -138,29 +138,33 @@ __device__ __forceinline__ long long to_fixed(uint32_t hi, uint32_t lo, const Fi
   return ((long long)m ^ sg) - sg;
 }
 
-// Double nearest toward zero to W * 2^(obias - 1086), sign flipped when neg = 1. |W| <= 2^62.
-static __device__ __noinline__ double from_fixed_small(unsigned long long a, uint32_t sign, const FixConv& cv) {
-  if (a == 0ull) return __hiloint2double((int)(sign << 31), 0);
+// |W| * 2^(obias - 1086) rounded toward zero, with sign bit `sign` (bit 31), or NaN for a NaN
+// class. The general path: zero, a small |W|, underflow.
+static __device__ __noinline__ double from_fixed_small(unsigned long long a, uint32_t sign, int obias, bool nan) {
+  if (nan) return f64_nan();
+  if (a == 0ull) return __hiloint2double((int)sign, 0);
   const int lz = __clzll((long long)a);
   const unsigned long long m = a << lz;  // leading one at bit 63
-  const int e = cv.obias - lz;
-  if (e <= 0) return __hiloint2double((int)(sign << 31), 0);  // below the normal range
+  const int e = obias - lz;
+  if (e <= 0) return __hiloint2double((int)sign, 0);  // below the normal range
   const uint32_t hi = (uint32_t)(m >> 43) + ((uint32_t)(e - 1) << 20);
-  return __hiloint2double((int)(hi | (sign << 31)), (int)(uint32_t)(m >> 11));
+  return __hiloint2double((int)(hi | sign), (int)(uint32_t)(m >> 11));
 }
-__device__ __forceinline__ double from_fixed(long long W, const FixConv& cv, uint32_t neg) {
+// Double nearest toward zero to W * 2^(obias - 1086), its sign bit XORed with negbit (0 or
+// 1 << 31). |W| <= 2^62.
+__device__ __forceinline__ double from_fixed(long long W, const FixConv& cv, uint32_t negbit) {
   const long long S = W >> 63;
   const unsigned long long a = (unsigned long long)((W ^ S) - S);
-  const uint32_t sign = ((uint32_t)S & 1u) ^ neg;
+  const uint32_t sign = ((uint32_t)((unsigned long long)W >> 32) ^ negbit) & 0x80000000u;
   const uint32_t ah = (uint32_t)(a >> 32);
-  if (ah == 0u || cv.slow) return from_fixed_small(a, sign, cv);
+  if (ah == 0u || cv.slow) return from_fixed_small(a, sign, cv.obias, cv.nan);
   // floor(log2(ah)) from the exponent of an exact-toward-zero float conversion
   const uint32_t fe = __float_as_uint(__uint2float_rz(ah)) >> 23;  // 127 + floor(log2 ah)
-  const uint32_t lz = 158u - fe;                                    // leading zeros of a (1..31)
-  const unsigned long long m = a << lz;                             // leading one at bit 63
-  // exponent field = obias - lz = obias - 158 + fe; the implicit one at bit 20 adds 1
-  const uint32_t hi = (uint32_t)(m >> 43) + (fe << 20) + cv.oexp;
-  return __hiloint2double((int)(hi | (sign << 31)), (int)(uint32_t)(m >> 11));
+  const unsigned long long m = a << (158u - fe);                    // leading one at bit 63
+  // exponent field = obias - 158 + fe; the implicit one at bit 20 adds 1; the sign is the
+  // top bit of a sum that stays below 2^31 without it
+  const uint32_t hi = (uint32_t)(m >> 43) + (fe << 20) + (cv.oexp + sign);
+  return __hiloint2double((int)hi, (int)(uint32_t)(m >> 11));
 }
 
 // popc(x & y) for a compile-time y with few bits: x's bits at those positions, pre-extracted
@@ -214,7 +218,7 @@ struct ArC128 {
     c.rbase = 1075 - s + lpre;
     c.obias = 1086 + out_scale_exp - s;  // 1023 + 63 + scale
     c.oexp = (uint32_t)(c.obias - 158 - 1) << 20;
-    c.slow = c.rbase < 64 || c.obias <= 64;
+    c.slow = c.rbase < 64 || c.obias <= 64 || c.nan;
     return c;
   }
   // Converted element times i^k (k mod 4).
@@ -241,14 +245,14 @@ struct ArC128 {
   __device__ static __forceinline__ Elem unpack(const uint4& q) {
     return Elem{(long long)(((unsigned long long)q.y << 32) | q.x), (long long)(((unsigned long long)q.w << 32) | q.z)};
   }
-  // W * 2^scale * i^k as a double pair.
+  // W * 2^scale * i^k as a double pair (NaN for a NaN class).
   __device__ static __forceinline__ double2 out_value(const Elem& a, const Conv& cv, uint32_t k) {
     const bool swap = k & 1u;
     const long long x = swap ? a.im : a.re, y = swap ? a.re : a.im;
+    const uint32_t k31 = k << 31, k30 = k << 30;  // bits 0 and 1 of k at bit 31
     double2 o;
-    o.x = from_fixed(x, cv, (k ^ (k >> 1)) & 1u);
-    o.y = from_fixed(y, cv, (k >> 1) & 1u);
-    if (cv.nan) o.x = o.y = f64_nan();
+    o.x = from_fixed(x, cv, k31 ^ k30);  // negated for k = 1, 2
+    o.y = from_fixed(y, cv, k30);         // negated for k = 2, 3
     return o;
   }
   __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
