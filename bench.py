@@ -67,7 +67,8 @@ def measured_peak_hbm():
 
 def source_hash():
     h = hashlib.sha256()
-    for name in ("xordiag.cu", "xordiag_impl.cuh", "xordiag_kernels.cuh", "xordiag_c128_decompose.cu", "common.cuh"):
+    for name in ("tiled_impl.cuh", "tiled.cu", "tiled.h", "tiled_c128_r3.cu", "xordiag.cu", "xordiag_impl.cuh",
+                 "common.cuh"):
         with open(os.path.join(ROOT, "paper_2401_16378_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -167,6 +168,19 @@ def oracle_rate(G, N, seconds_target, seed=4242):
     return k / dt, k, dt, threads
 
 
+def metric_name(N):
+    return f"Pauli coefficients per second, N={N} complex128"
+
+
+def workload_config(N, world):
+    """The `config` object of both arms' JSON lines."""
+    D = 1 << N
+    return {"workload": f"N={N}: {D}x{D} complex128 dense matrix, i.i.d. complex normal entries "
+                        f"(seed {14 if N == 14 else N}), all 4^{N} coefficients", "N": N,
+            "matrix_bytes": 16 * 4 ** N, "l2": "inputs larger than L2 (no flush needed)", "io_dtype": "complex128",
+            "parallelism": f"replicas x{world}"}
+
+
 # --------------------------------------------------------------------------- reference arm --
 def run_reference(args):
     world, rank, _ = dist_env()
@@ -195,12 +209,11 @@ def run_reference(args):
         total_k += k
     value = total_k / total_t
     sample = f"{k} seeded random coefficients of the N={N} matrix per step (O(2^N) each, Eq. (13))"
-    line = {"impl": "reference", "metric": f"Pauli coefficients per second, N={N} complex128", "value": value,
+    line = {"impl": "reference", "metric": metric_name(N), "value": value,
             "unit": "coeffs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"N={N}: {1 << N}x{1 << N} complex128, i.i.d. complex normal, seed 14",
-                       "N": N},
+            "config": workload_config(N, world),
             "cpu_baseline": {"value": value, "unit": "coeffs/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "coeffs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -324,14 +337,11 @@ def run_ours(args):
     cpu = {"value": rate, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
            "sample": f"{k} seeded random coefficients of the N={N} workload in {dt:.1f} s (Eq. (13), O(2^N) each)"}
 
-    line = {"metric": f"Pauli coefficients per second, N={N} complex128 (XOR-diagonal + WHT)", "value": value,
+    line = {"metric": metric_name(N), "value": value,
             "unit": "coeffs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {"workload": f"N={N}: {D}x{D} complex128 dense matrix, i.i.d. complex normal entries "
-                                   f"(seed 14), all 4^{N} coefficients", "N": N, "matrix_bytes": ncoef * es,
-                       "l2": "inputs larger than L2 (no flush needed)", "io_dtype": "complex128",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(N, world),
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": world * ncoef / (e2e_ms * 1e-3), "unit": "coeffs/s",
                     "h2d_bytes_per_step": ncoef * es, "d2h_bytes_per_step": ncoef * es},

@@ -67,7 +67,11 @@ typedef enum {
 /* Decompose `count` matrices of N qubits (1 <= N <= PAULI_MAX_QUBITS, count >= 1) stored
  * contiguously at G into 4^N coefficients each, stored contiguously at out.
  *   out[k * 4^N + n] = c_n of matrix k = 2^-N Tr(P_n G_k)              Eq. (4), via Eq. (13).
- * dtype applies to both G and out. method: pauli_method. */
+ * dtype applies to both G and out. method: pauli_method.
+ * With PAULI_XORDIAG at N = 13 and 14 the built-in launch shape is PAULI_VARIANT_TILED8 (see
+ * below), which allocates a scratch buffer of 3 x 2^(N+10) bytes (plus about 1 MiB) with
+ * cudaMalloc at its first use on each (device, stream) pair and keeps it: make the first such
+ * call on a stream before capturing that stream into a CUDA graph. */
 int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int method, void* stream);
 
 /* Compose: G_out[k] = 2^scale_exp * sum_n c[k * 4^N + n] P_n                         Eq. (1).

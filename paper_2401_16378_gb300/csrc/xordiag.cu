@@ -55,7 +55,14 @@ constexpr long long kTiledMaxCount = 1024;
 // Chosen variant per (N, dtype, direction): 0 = built-in default. Set by the autotuner.
 int g_variant[2][2][17];
 
-int default_variant(int N) { return N >= 7 ? kVariantUnit13 : kVariantUnit12; }
+// Built-in choice: the two-stage tiled kernel for decompositions at N = 13, 14 (measured
+// faster there on GB300), else single-pass units of 8192 (4096 below N = 7) elements.
+int default_variant(int N, bool compose) {
+  if (!compose && (N == 13 || N == 14)) return kVariantTiled8;
+  return N >= 7 ? kVariantUnit13 : kVariantUnit12;
+}
+// The single-pass choice, for requests the tiled kernel cannot take.
+int single_pass_variant(int N) { return N >= 7 ? kVariantUnit13 : kVariantUnit12; }
 
 }  // namespace
 
@@ -66,7 +73,7 @@ bool xordiag_variant_supported(int variant, int N, bool compose) { return varian
 int xordiag_get_variant(int N, bool c64, bool compose) {
   if (N < 0 || N > 16) return 0;
   const int v = g_variant[c64][compose][N];
-  return v ? v : (xordiag_supported(N) ? default_variant(N) : 0);
+  return v ? v : (xordiag_supported(N) ? default_variant(N, compose) : 0);
 }
 
 void xordiag_set_variant(int N, bool c64, bool compose, int variant) {
@@ -79,13 +86,13 @@ cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, boo
     variant = xordiag_get_variant(N, c64, compose);
     if ((variant == kVariantTiled8 || variant == kVariantTiled16) &&
         (count > kTiledMaxCount || (reinterpret_cast<uintptr_t>(in) & 15u)))
-      variant = default_variant(N);
+      variant = single_pass_variant(N);
   }
   if (!variant_has(variant, N, compose)) return cudaErrorNotSupported;
   if (variant == kVariantTiled8 || variant == kVariantTiled16) {
     // the bulk copies need 16-byte aligned sources: other G take the single-pass kernel
     if (count > kTiledMaxCount || (reinterpret_cast<uintptr_t>(in) & 15u))
-      return launch_xordiag(in, N, count, c64, compose, scale_exp, out, s, default_variant(N));
+      return launch_xordiag(in, N, count, c64, compose, scale_exp, out, s, single_pass_variant(N));
     return launch_tiled(in, N, (int)count, c64, out, variant == kVariantTiled8 ? 3 : 4, s);
   }
   if (c64)
