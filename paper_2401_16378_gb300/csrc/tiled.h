@@ -7,7 +7,7 @@
 
 namespace pauli {
 
-constexpr int kTiledSlots = 3;  // scratch ring slots
+constexpr int kTiledSlots = 6;  // most scratch ring slots (the ring depth is chosen per N)
 
 // Device control block at the start of the workspace. Everything from `counter` on is
 // cleared before every launch; `status` keeps the first error until pauli_stream_status reads
@@ -18,10 +18,10 @@ struct TiledCtrl {
   int counter;                  // next work item
   int s1_done[kTiledSlots];     // stage-1 tiles completed per slot (all generations)
   int s2_done[kTiledSlots];     // stage-2 items that have copied their slot's data (all generations)
-  int pad1[5];
+  int pad1[7];
   uint32_t emax[kTiledSlots][64];  // per class of the slot's block: (generation + 1) << 11 | exponent
 };
-constexpr size_t kTiledCtrlBytes = 1024;  // control block, padded; the slots follow
+constexpr size_t kTiledCtrlBytes = 2048;  // control block, padded; the slots follow
 static_assert(sizeof(TiledCtrl) <= kTiledCtrlBytes, "control block fits its padding");
 
 bool tiled_supported(int N);

@@ -26,7 +26,7 @@
 //
 // The scratch is laid out so that each stage-2 item reads one contiguous 64 KiB chunk:
 // P[o][q][R][wl][c8] (octet o, w = (q << ZB) | wl, class 8o + c8), 16 bytes per entry,
-// then E[o][R][c8] (exponent key of each class in each tile). A ring of kTiledSlots slots
+// then E[o][R][c8] (exponent key of each class in each tile). A ring of Geo<N>::NS slots
 // holds 64 x 2^N partials each (16 MiB at N = 14); it is written with an L2 evict-last policy
 // and stays in L2 while G and c stream through with evict-first.
 //
@@ -90,7 +90,11 @@ struct Geo {
   static constexpr size_t kBuf = kChunk + kEOct + 128;  // buffer: data, E, class maxima
   static constexpr size_t kSlotP = (size_t)16 << (N + kCB);
   static constexpr size_t kSlot = kSlotP + (size_t)NR * 64 * 4;
-  static constexpr size_t kWorkspace = kTiledCtrlBytes + kTiledSlots * kSlot;
+  // ring depth: enough blocks in flight for the items the CTAs hold (152 x 3 buffers), within
+  // about 48 MiB of L2
+  static constexpr int NS = N <= 12 ? 6 : N == 13 ? 5 : 3;
+  static_assert(NS <= kTiledSlots, "control block has room for the ring");
+  static constexpr size_t kWorkspace = kTiledCtrlBytes + NS * kSlot;
   static_assert(ZB >= 0 && L >= 4, "12 <= N <= 15");
   static_assert(n1 == n2, "both stages have 2^L items per block");
 };
@@ -242,7 +246,7 @@ __device__ void producer(const CUtensorMap* map, int count, TiledCtrl* ws, Share
     if (use >= kBufs && !wait_phase(smem_addr(&sh.empty[buf]), ((use / kBufs) - 1) & 1, &ws->status))
       break;  // the consumers never released the buffer: they give up on their own wait
     bool ok = true;
-    const int s = done ? 0 : it.b % kTiledSlots, gen = done ? 0 : it.b / kTiledSlots;
+    const int s = done ? 0 : it.b % GE::NS, gen = done ? 0 : it.b / GE::NS;
     if (!done) {  // dependencies: the slot must be free (stage 1) or complete (stage 2)
       if (it.s1) {
         if (gen > 0) ok = wait_count(&ws->s2_done[s], GE::n2 * gen, &ws->status);
@@ -522,7 +526,7 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
     if (item < 0) break;
     Item<N> it;
     it.decode(item, blocks);
-    const int s = it.b % kTiledSlots, gen = it.b / kTiledSlots;
+    const int s = it.b % GE::NS, gen = it.b / GE::NS;
     const uint32_t addr = buf0 + (uint32_t)(buf * GE::kBuf);
     if (t == 0) sh.rel_slot[buf] = it.s1 ? s : -1;
     if (it.s1) {
