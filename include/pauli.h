@@ -68,10 +68,10 @@ typedef enum {
  * contiguously at G into 4^N coefficients each, stored contiguously at out.
  *   out[k * 4^N + n] = c_n of matrix k = 2^-N Tr(P_n G_k)              Eq. (4), via Eq. (13).
  * dtype applies to both G and out. method: pauli_method.
- * With PAULI_XORDIAG at N = 13 and 14 the built-in launch shape is PAULI_VARIANT_TILED8 (see
- * below), which allocates a scratch buffer of 3 x 2^(N+10) bytes (plus about 1 MiB) with
- * cudaMalloc at its first use on each (device, stream) pair and keeps it: make the first such
- * call on a stream before capturing that stream into a CUDA graph. */
+ * With PAULI_XORDIAG at N = 13 and 14 the built-in launch shape is a tiled one (see
+ * PAULI_VARIANT_TILED8 below), which allocates a scratch buffer (48 MiB at N = 14, 40 MiB at
+ * N = 13) with cudaMalloc at its first use on each (device, stream) pair and keeps it: make
+ * the first such call on a stream before capturing that stream into a CUDA graph. */
 int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int method, void* stream);
 
 /* Compose: G_out[k] = 2^scale_exp * sum_n c[k * 4^N + n] P_n                         Eq. (1).
@@ -154,18 +154,20 @@ void pauli_plan_destroy(pauli_plan* plan);
  *                           64-element run of G) and does the 6 low transform stages; stage 2
  *                           the other N - 6. One persistent, warp-specialised launch (a copy
  *                           warp feeding 512 compute threads, 8 elements each, through a ring
- *                           of shared-memory buffers). The scratch (3 x 2^(N+10) bytes plus
- *                           about 1 MiB) is allocated with cudaMalloc at the first call on each
+ *                           of shared-memory buffers). The scratch (S x 2^(N+10) bytes plus
+ *                           a little, S = 6, 5, 3 slots at N = 12, 13, 14) is allocated with cudaMalloc at the first call on each
  *                           (device, stream) pair and kept until the process exits: make that
  *                           first call before capturing the stream into a graph. Calls on one
  *                           stream are ordered by the stream; calls on different streams get
  *                           different scratch.
- * PAULI_VARIANT_TILED16:    the same with 256 compute threads of 16 elements each.
+ * PAULI_VARIANT_TILED16:    the same with two groups of 256 compute threads of 16 elements
+ *                           each, working on alternate buffers.
  * All variants compute bit-identical complex128 results, except that the tiled ones re-scale
  * partial sums between the stages (an extra truncation below the class quantum, well inside
- * the accuracy bound of pauli_decompose); they differ otherwise only in speed. The choice is process-wide per (N, dtype, op), op 0 =
- * decompose, 1 = compose; variant 0 restores the built-in default. The autotuner in the
- * Python package measures both and records its choice here. */
+ * the accuracy bound of pauli_decompose); they differ otherwise only in speed. The choice is
+ * process-wide per (N, dtype, op), op 0 = decompose, 1 = compose; variant 0 restores the
+ * built-in default. The autotuner in the Python package measures the variants and records
+ * its choice here. */
 #define PAULI_VARIANT_DEFAULT 0
 #define PAULI_VARIANT_UNIT8192 1
 #define PAULI_VARIANT_UNIT4096 2

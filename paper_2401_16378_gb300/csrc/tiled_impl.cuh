@@ -27,25 +27,27 @@
 // The scratch is laid out so that each stage-2 item reads one contiguous 64 KiB chunk:
 // P[o][q][R][wl][c8] (octet o, w = (q << ZB) | wl, class 8o + c8), 16 bytes per entry,
 // then E[o][R][c8] (exponent key of each class in each tile). A ring of Geo<N>::NS slots
-// holds 64 x 2^N partials each (16 MiB at N = 14); it is written with an L2 evict-last policy
-// and stays in L2 while G and c stream through with evict-first.
+// holds 64 x 2^N partials each (16 MiB at N = 14; 3 to 6 slots by N); it is written with an L2
+// evict-last policy and stays in L2 while G and c stream through with evict-first.
 //
 // Launch: one persistent CTA per SM, warp-specialised.
-//  - a producer warp takes work items from a global counter in the order S1(block 0), S1(1),
-//    S2(0), S1(2), S2(1), ..., waits for the item's dependencies (a stage-2 item needs the 2^L
-//    tiles of its block; a stage-1 item needs the stage-2 items of the block that last used its
-//    slot to have copied their data out), and fills a 3-deep ring of shared-memory buffers: one
-//    2D TMA tensor load per stage-1 tile (64 rows of 64 elements), one bulk copy per stage-2
-//    chunk, completing on the buffer's mbarrier;
-//  - the consumer warps (512 threads x 8 elements or 256 x 16) take the buffers in order,
-//    compute and store; each warp hands the buffer back (mbarrier) as soon as it is done with it;
+//  - a producer warp takes work items from a global counter in the order S1(block 0), ...,
+//    S1(LAG), S2(0), S1(LAG + 1), S2(1), ..., waits for the item's dependencies (a stage-2 item
+//    needs the 2^L tiles of its block; a stage-1 item needs the stage-2 items of the block that
+//    last used its slot to have copied their data out), and fills a 3-deep ring of
+//    shared-memory buffers: one 2D TMA tensor load per stage-1 tile (64 rows of 64 elements),
+//    one bulk copy per stage-2 chunk, completing on the buffer's mbarrier;
+//  - the consumers take the buffers in order: one group of 512 threads x 8 elements, or two
+//    groups of 256 threads x 16 elements that take alternate buffers (so that one group's
+//    arithmetic overlaps the other's shared-memory phases); each warp hands the buffer back
+//    (mbarrier) as soon as it is done with it;
 //  - a release warp publishes each finished stage-1 tile to the other SMs (a release reduction
 //    on the slot's counter, which waits for the tile's stores to reach L2) off the consumers'
 //    critical path.
-// Loads for the next two items are in flight while one is computed.
 //
-// Every item waited on was taken from the counter earlier by a CTA that processes its items in
-// the order it took them, so every wait ends. Each wait is bounded nevertheless: after
+// Every item waited on was taken from the counter earlier (the producer takes items in
+// order), and an item whose copies a CTA has issued is finished by its consumers without
+// waiting on any other item, so every wait ends. Each wait is bounded nevertheless: after
 // kPolls polls the waiting thread records PAULI_ERR_TIMEOUT in the status word, the CTA stops
 // taking work, waits (bounded) for its copies in flight and exits; the results are then invalid.
 #pragma once
@@ -94,6 +96,12 @@ struct Geo {
   // about 48 MiB of L2
   static constexpr int NS = N <= 12 ? 6 : N == 13 ? 5 : 3;
   static_assert(NS <= kTiledSlots, "control block has room for the ring");
+  // stage-2 items of block b follow stage-1 tiles of block b + LAG in the work order, so that
+  // block b's tiles are finished by the time its stage-2 items are taken; a stage-1 tile of
+  // block b reuses the slot of block b - NS, whose stage-2 items come LAG - NS + 1 <= -1 groups
+  // earlier
+  static constexpr int LAG = N <= 12 ? 3 : N == 13 ? 2 : 1;
+  static_assert(NS >= LAG + 2, "slot reuse waits on items taken at least a group earlier");
   static constexpr size_t kWorkspace = kTiledCtrlBytes + NS * kSlot;
   static_assert(ZB >= 0 && L >= 4, "12 <= N <= 15");
   static_assert(n1 == n2, "both stages have 2^L items per block");
@@ -174,11 +182,20 @@ struct Shared {
   uint64_t done[kBufs];   // item's stores issued: one arrival per consumer warp (release warp waits)
   int item[kBufs];        // work item in the buffer, -1 = no more work
   int rel_slot[kBufs];    // per buffer use: slot to publish (stage 1), -1 (stage 2), -2 (end)
-  int ok;                 // consumers: the next buffer arrived (broadcast by consumer 0)
-  int waited;             // buffer uses whose data consumer 0 has waited for
-  int issued;             // buffer uses whose copies the producer has issued
+  int ok[2];              // per consumer group: its next buffer arrived (broadcast by its thread 0)
+  int waited_use[kBufs];  // per buffer: the last use whose data a consumer group waited for
+  int issued_use[kBufs];  // per buffer: the last use whose copies the producer issued
   int released;           // buffer uses the release warp has handled
-  uint32_t smax[64];      // stage 1: (use + 1) << 11 | largest exponent of each class
+  uint32_t smax[2][64];   // stage 1, per group: (use + 1) << 11 | largest exponent of each class
+};
+
+// Named barrier of one consumer group (ID 1 + group, THREADS threads).
+template <int THREADS>
+struct GroupBar {
+  uint32_t id;
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(THREADS) : "memory");
+  }
 };
 
 // Bounded wait on an mbarrier phase; false (status recorded) when it gave up.
@@ -198,8 +215,9 @@ __device__ __forceinline__ bool wait_count(const int* counter, int target, int* 
   return false;
 }
 
-// Work item -> (stage, block, index within the block); false for the padding items of the
-// order (stage 1 past the last block, stage 2 before the first).
+// Work item -> (stage, block, index within the block). Group g of the order holds the
+// stage-1 tiles of block g, then the stage-2 items of block g - LAG; false for the padding
+// items (stage 1 past the last block, stage 2 before the first).
 template <int N>
 struct Item {
   bool s1;
@@ -208,9 +226,9 @@ struct Item {
     constexpr int group = Geo<N>::n1 + Geo<N>::n2;
     const int g = item / group, r = item % group;
     s1 = r < Geo<N>::n1;
-    b = s1 ? g : g - 1;
+    b = s1 ? g : g - Geo<N>::LAG;
     j = s1 ? r : r - Geo<N>::n1;
-    return s1 ? g < blocks : g > 0;
+    return s1 ? g < blocks : b >= 0;
   }
 };
 
@@ -219,7 +237,7 @@ __device__ __forceinline__ char* slot_base(TiledCtrl* ws, size_t slot_bytes, int
 }
 
 // ---------------------------------------------------------------------- producer --
-template <int N, class AR>
+template <int N, class AR, int GROUPS>
 __device__ void producer(const CUtensorMap* map, int count, TiledCtrl* ws, Shared& sh, uint32_t buf0) {
   using GE = Geo<N>;
   constexpr uint32_t D = 1u << N;
@@ -228,7 +246,7 @@ __device__ void producer(const CUtensorMap* map, int count, TiledCtrl* ws, Share
   constexpr int kX = (int)sizeof(typename AR::Raw) / 8;  // map elements per matrix element
   const int lane = threadIdx.x & 31;
   const int blocks = nb * count;
-  const int n_items = (blocks + 1) * (GE::n1 + GE::n2);
+  const int n_items = (blocks + GE::LAG) * (GE::n1 + GE::n2);
   const uint64_t pol_first = policy_evict_first();
   if (lane != 0) return;  // one thread drives the ring
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
@@ -256,9 +274,15 @@ __device__ void producer(const CUtensorMap* map, int count, TiledCtrl* ws, Share
         asm volatile("fence.proxy.async.global;" ::: "memory");
       }
     }
-    if (done || !ok) {  // no more work (or a dependency never came): tell the consumers
+    if (done || !ok) {  // no more work (or a dependency never came): one end mark per group
       sh.item[buf] = -1;
       mbar_arrive(full);
+      for (int g = 1; g < GROUPS; ++g) {
+        const int u = use + g, b = u % kBufs;
+        if (u >= kBufs && !wait_phase(smem_addr(&sh.empty[b]), ((u / kBufs) - 1) & 1, &ws->status)) break;
+        sh.item[b] = -1;
+        mbar_arrive(smem_addr(&sh.full[b]));
+      }
       break;
     }
     const uint32_t dst = buf0 + (uint32_t)(buf * GE::kBuf);
@@ -277,8 +301,8 @@ __device__ void producer(const CUtensorMap* map, int count, TiledCtrl* ws, Share
                pol_first);
       bulk_g2s(dst + (uint32_t)(GE::kChunk + GE::kEOct), &ws->emax[s][o * 8], 32u, full, pol_first);
     }
+    sh.issued_use[buf] = use;
     ++use;
-    sh.issued = use;
   }
 }
 
@@ -338,11 +362,11 @@ __host__ __device__ constexpr uint32_t s1_load_off(int j) {
 
 // Tile R of block k in the buffer: element (i, c) at slot (i << 6) | (i ^ c).
 template <int N, int RB, class AR, int CT>
-__device__ __forceinline__ void stage1(uint32_t tile, const S1Thread<RB, N>& th, char* slot, TiledCtrl* ws, int s,
-                                       int gen, uint32_t R, Shared& sh, uint32_t tag, uint64_t pol_keep) {
+__device__ __forceinline__ void stage1(uint32_t tile, const S1Thread<RB, N>& th, uint32_t tg, const GroupBar<CT>& bar,
+                                       char* slot, TiledCtrl* ws, int s, int gen, uint32_t R, uint32_t* smax,
+                                       uint32_t tag, uint64_t pol_keep) {
   using GE = Geo<N>;
   using LY = Layout<kUB, kTB, RB>;
-  using SY = NamedSync<1, CT>;
   static_assert(LY::K == kCB, "tile = 64 classes x 64 rows");
   constexpr int E = LY::E;
   constexpr uint32_t kEs = sizeof(typename AR::Raw);
@@ -362,10 +386,10 @@ __device__ __forceinline__ void stage1(uint32_t tile, const S1Thread<RB, N>& th,
   }
   uint32_t Ekey = 0;
   if constexpr (AR::kScaled) {
-    atomicMax(&sh.smax[th.c], (tag << 11) | (emax >> 20));  // older tags are smaller: no reset needed
+    atomicMax(&smax[th.c], (tag << 11) | (emax >> 20));  // older tags are smaller: no reset needed
   }
-  SY::sync();  // exponents complete, and every tile read is done: the buffer serves the exchange
-  if constexpr (AR::kScaled) Ekey = (sh.smax[th.c] & 0x7FFu) << 20;
+  bar.sync();  // exponents complete, and every tile read is done: the buffer serves the exchange
+  if constexpr (AR::kScaled) Ekey = (smax[th.c] & 0x7FFu) << 20;
   const typename AR::Conv cv = AR::make_conv(N, Ekey, 0);
   typename AR::Elem v[E];
 #pragma unroll
@@ -375,7 +399,7 @@ __device__ __forceinline__ void stage1(uint32_t tile, const S1Thread<RB, N>& th,
 #pragma unroll
   for (int j = 0; j < E; ++j)
     sts128(tile + 16u * (th.xw ^ (LY::reg_u(0, j) ^ swz_term(LY::reg_u(0, j)))), AR::pack(v[j]));
-  SY::sync();
+  bar.sync();
 #pragma unroll
   for (int j = 0; j < E; ++j)
     v[j] = AR::unpack(lds128(tile + 16u * (th.xr ^ (LY::reg_u(1, j) ^ swz_term(LY::reg_u(1, j))))));
@@ -384,10 +408,10 @@ __device__ __forceinline__ void stage1(uint32_t tile, const S1Thread<RB, N>& th,
   uint4* P = reinterpret_cast<uint4*>(slot) + th.st + (R << (GE::ZB + 3));
 #pragma unroll
   for (int j = 0; j < E; ++j) st_hint(P + s1_store_off<LY, N>(j), AR::pack(v[j]), pol_keep);
-  if (threadIdx.x < 64) {
+  if (tg < 64) {
     uint32_t* Ep = reinterpret_cast<uint32_t*>(slot + GE::kSlotP);
-    Ep[((threadIdx.x >> 3) * GE::NR + R) * 8 + (threadIdx.x & 7u)] = Ekey;
-    if constexpr (AR::kScaled) red_max(&ws->emax[s][threadIdx.x], ((uint32_t)(gen + 1) << 11) | (Ekey >> 20));
+    Ep[((tg >> 3) * GE::NR + R) * 8 + (tg & 7u)] = Ekey;
+    if constexpr (AR::kScaled) red_max(&ws->emax[s][tg], ((uint32_t)(gen + 1) << 11) | (Ekey >> 20));
   }
 }
 
@@ -415,19 +439,20 @@ struct S2Thread {
   }
 };
 
-template <class LY, class AR, class SY, int P>
-__device__ __forceinline__ void s2_phases(typename AR::Elem (&v)[LY::E], uint32_t xaddr, const uint32_t* ex) {
+template <class LY, class AR, class BAR, int P>
+__device__ __forceinline__ void s2_phases(typename AR::Elem (&v)[LY::E], uint32_t xaddr, const uint32_t* ex,
+                                          const BAR& bar) {
   wht_regs<AR, LY::gcount(P), LY::E>(v);
   if constexpr (P + 1 < LY::NPH) {
-    SY::sync();  // previous reads of the buffer are done
+    bar.sync();  // previous reads of the buffer are done
 #pragma unroll
     for (int j = 0; j < LY::E; ++j)
       sts128(xaddr + 16u * (ex[2 * P] ^ (LY::reg_u(P, j) ^ swz_term(LY::reg_u(P, j)))), AR::pack(v[j]));
-    SY::sync();
+    bar.sync();
 #pragma unroll
     for (int j = 0; j < LY::E; ++j)
       v[j] = AR::unpack(lds128(xaddr + 16u * (ex[2 * P + 1] ^ (LY::reg_u(P + 1, j) ^ swz_term(LY::reg_u(P + 1, j))))));
-    s2_phases<LY, AR, SY, P + 1>(v, xaddr, ex);
+    s2_phases<LY, AR, BAR, P + 1>(v, xaddr, ex, bar);
   }
 }
 
@@ -436,11 +461,10 @@ __device__ __forceinline__ void s2_phases(typename AR::Elem (&v)[LY::E], uint32_
 // eight tagged class maxima.
 template <int N, int RB, class AR, int CT>
 __device__ __forceinline__ void stage2(uint32_t chunk, const char* chunk_gen, const S2Thread<RB, N>& th,
-                                       void* __restrict__ out, unsigned long long obase, uint32_t k, uint32_t item,
-                                       uint64_t pol_out) {
+                                       const GroupBar<CT>& bar, void* __restrict__ out, unsigned long long obase,
+                                       uint32_t k, uint32_t item, uint64_t pol_out) {
   using GE = Geo<N>;
   using LY = Layout<kUB, GE::L, RB>;
-  using SY = NamedSync<1, CT>;
   constexpr int K = LY::K, E = LY::E, LAST = LY::NPH - 1, ZB = GE::ZB;
   static_assert(K == GE::K2, "stage-2 unit = 8 classes x 2^ZB w x 2^L row blocks");
   const uint32_t o = item & 7u, q = item >> 3;
@@ -466,7 +490,7 @@ __device__ __forceinline__ void stage2(uint32_t chunk, const char* chunk_gen, co
   } else {
     cv = AR::make_conv(N, 0u, -N);
   }
-  s2_phases<LY, AR, SY, 0>(v, chunk, th.ex);  // the first barrier also ends the chunk reads
+  s2_phases<LY, AR, GroupBar<CT>, 0>(v, chunk, th.ex, bar);  // the first barrier also ends the chunk reads
   // c(x, z), z = (h << 6) | w, h = ht | (register part)
   Addr<N, false> ao;
   ao.init(obase, x, (th.ht << kTB) | w);
@@ -483,28 +507,30 @@ __device__ __forceinline__ void stage2(uint32_t chunk, const char* chunk_gen, co
 }
 
 // ---------------------------------------------------------------------- consumers --
-template <int N, int RB, class AR, int CT>
+// Consumer group `g` (CT threads) takes the buffer uses g, g + GROUPS, g + 2 GROUPS, ...
+template <int N, int RB, class AR, int CT, int GROUPS>
 __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Shared& sh, char* bufs, uint32_t buf0) {
   using GE = Geo<N>;
-  using SY = NamedSync<1, CT>;
   constexpr uint32_t D = 1u << N;
   constexpr int nb = 1 << (N - kCB);
-  const uint32_t t = threadIdx.x, lane = t & 31u;
+  const uint32_t g = threadIdx.x / CT, tg = threadIdx.x % CT, lane = threadIdx.x & 31u;
+  const GroupBar<CT> bar{1u + g};
   const int blocks = nb * count;
   const uint64_t pol_keep = policy_evict_last(), pol_first = policy_evict_first();
   S1Thread<RB, N> t1;
   S2Thread<RB, N> t2;
-  t1.init(t);
-  t2.init(t);
+  t1.init(tg);
+  t2.init(tg);
   volatile int* released = &sh.released;
-  int use = 0;
-  for (;; ++use) {
+  int use = (int)g;
+  for (;; use += GROUPS) {
     const int buf = use % kBufs;
     const uint32_t full = smem_addr(&sh.full[buf]);
     const uint32_t parity = (use / kBufs) & 1;
-    // consumer 0 waits (bounded) and broadcasts, so that all consumers leave together; it also
-    // keeps the release warp less than a ring behind (its barrier phases must not be lapped)
-    if (t == 0) {
+    // the group's thread 0 waits (bounded) and broadcasts, so that the group leaves together;
+    // it also keeps the release warp less than a ring behind (its barrier phases must not be
+    // lapped, and it reads rel_slot[] of the use a ring earlier)
+    if (tg == 0) {
       bool ok = true;
       for (int i = 0; *released < use - kBufs + 1; ++i) {
         if (i == kPolls) {
@@ -515,11 +541,11 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
         __nanosleep(64);
       }
       ok = ok && wait_phase(full, parity, &ws->status);
-      if (ok) sh.waited = use + 1;
-      sh.ok = ok;
+      if (ok) sh.waited_use[buf] = use;
+      sh.ok[g] = ok;
     }
-    SY::sync();
-    if (!sh.ok) break;
+    bar.sync();
+    if (!sh.ok[g]) break;
     for (int i = 0; i < kPolls && !mbar_try_wait(full, parity); ++i) {  // completes at once: acquires the data
     }
     const int item = sh.item[buf];
@@ -528,15 +554,15 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
     it.decode(item, blocks);
     const int s = it.b % GE::NS, gen = it.b / GE::NS;
     const uint32_t addr = buf0 + (uint32_t)(buf * GE::kBuf);
-    if (t == 0) sh.rel_slot[buf] = it.s1 ? s : -1;
+    if (tg == 0) sh.rel_slot[buf] = it.s1 ? s : -1;
     if (it.s1) {
-      stage1<N, RB, AR, CT>(addr, t1, slot_base(ws, GE::kSlot, s), ws, s, gen, (uint32_t)it.j, sh, (uint32_t)use + 1u,
-                            pol_keep);
+      stage1<N, RB, AR, CT>(addr, t1, tg, bar, slot_base(ws, GE::kSlot, s), ws, s, gen, (uint32_t)it.j, sh.smax[g],
+                            (uint32_t)use + 1u, pol_keep);
     } else {
       // the slot's data is in shared memory: a relaxed count suffices (the copy has completed)
-      if (t == 0) red_relaxed_add(&ws->s2_done[s], 1);
-      stage2<N, RB, AR, CT>(addr, bufs + (size_t)buf * GE::kBuf, t2, out, (unsigned long long)(it.b / nb) * D * D,
-                            (uint32_t)(it.b % nb), (uint32_t)it.j, pol_first);
+      if (tg == 0) red_relaxed_add(&ws->s2_done[s], 1);
+      stage2<N, RB, AR, CT>(addr, bufs + (size_t)buf * GE::kBuf, t2, bar, out,
+                            (unsigned long long)(it.b / nb) * D * D, (uint32_t)(it.b % nb), (uint32_t)it.j, pol_first);
     }
     // this warp is done with the buffer and has issued its stores
     __syncwarp();
@@ -547,25 +573,31 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
       mbar_arrive(smem_addr(&sh.done[buf]));
     }
   }
-  // tell the release warp to stop: a last done phase marked -2 (after the previous uses'
-  // phases, which every warp has arrived on)
+  // tell the release warp to stop: a done phase marked -2 (after the previous uses' phases,
+  // which every warp of their groups has arrived on)
   const int buf = use % kBufs;
-  if (t == 0) sh.rel_slot[buf] = -2;
-  SY::sync();
+  if (tg == 0) sh.rel_slot[buf] = -2;
+  bar.sync();
   if (lane == 0) mbar_arrive(smem_addr(&sh.done[buf]));
 }
 
+// 8 elements per thread: one group of 512 consumer threads; 16 per thread: two groups of
+// 256, each on its own work item.
 template <int RB>
 struct TiledShape {
-  static constexpr int kConsumers = 1 << (kUB - RB);
-  static constexpr int kWarps = kConsumers / 32;
+  static constexpr int kGroups = RB == 4 ? 2 : 1;
+  static constexpr int kGroupThreads = 1 << (kUB - RB);
+  static constexpr int kConsumers = kGroups * kGroupThreads;
+  static constexpr int kGroupWarps = kGroupThreads / 32;
   static constexpr int kThreads = kConsumers + 64;  // + producer warp + release warp
 };
 
 template <int N, int RB, class AR>
 __global__ void __launch_bounds__(TiledShape<RB>::kThreads, 1)
     tiled_kernel(const __grid_constant__ CUtensorMap map, void* __restrict__ out, int count, TiledCtrl* ws) {
-  constexpr int CT = TiledShape<RB>::kConsumers;
+  constexpr int CT = TiledShape<RB>::kGroupThreads;
+  constexpr int GROUPS = TiledShape<RB>::kGroups;
+  constexpr int CONSUMERS = TiledShape<RB>::kConsumers;
   extern __shared__ __align__(1024) char bufs[];
   __shared__ Shared sh;
   const uint32_t t = threadIdx.x;
@@ -573,20 +605,20 @@ __global__ void __launch_bounds__(TiledShape<RB>::kThreads, 1)
   if (t == 0) {
     for (int b = 0; b < kBufs; ++b) {
       mbar_init(smem_addr(&sh.full[b]), 1);
-      mbar_init(smem_addr(&sh.empty[b]), TiledShape<RB>::kWarps);
-      mbar_init(smem_addr(&sh.done[b]), TiledShape<RB>::kWarps);
+      mbar_init(smem_addr(&sh.empty[b]), TiledShape<RB>::kGroupWarps);  // one use = one group
+      mbar_init(smem_addr(&sh.done[b]), TiledShape<RB>::kGroupWarps);
+      sh.waited_use[b] = -1;
+      sh.issued_use[b] = -1;
     }
-    sh.waited = 0;
-    sh.issued = 0;
     sh.released = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (t < 64) sh.smax[t] = 0;
+  if (t < 128) sh.smax[t >> 6][t & 63] = 0;
   __syncthreads();
-  if (t < (uint32_t)CT) {
-    consumer<N, RB, AR, CT>(out, count, ws, sh, bufs, buf0);
-  } else if (t < (uint32_t)CT + 32) {
-    producer<N, AR>(&map, count, ws, sh, buf0);
+  if (t < (uint32_t)CONSUMERS) {
+    consumer<N, RB, AR, CT, GROUPS>(out, count, ws, sh, bufs, buf0);
+  } else if (t < (uint32_t)CONSUMERS + 32) {
+    producer<N, AR, GROUPS>(&map, count, ws, sh, buf0);
     __syncwarp();  // lane 0 drove the ring alone; the barrier below wants whole warps
   } else {
     releaser(ws, sh);
@@ -594,10 +626,12 @@ __global__ void __launch_bounds__(TiledShape<RB>::kThreads, 1)
   }
   __syncthreads();
   // after a wait gave up: wait (bounded) for copies still landing in buffers nobody waited for
-  if (t == (uint32_t)CT && sh.issued > sh.waited) {
-    for (int use = sh.waited; use < sh.issued; ++use) {
-      const uint32_t full = smem_addr(&sh.full[use % kBufs]);
-      for (int i = 0; i < kPolls && !mbar_try_wait(full, (use / kBufs) & 1); ++i) {
+  if (t == (uint32_t)CONSUMERS) {
+    for (int b = 0; b < kBufs; ++b) {
+      const int u = sh.issued_use[b];
+      if (u <= sh.waited_use[b]) continue;
+      const uint32_t full = smem_addr(&sh.full[b]);
+      for (int i = 0; i < kPolls && !mbar_try_wait(full, (u / kBufs) & 1); ++i) {
       }
     }
   }

@@ -55,10 +55,12 @@ constexpr long long kTiledMaxCount = 1024;
 // Chosen variant per (N, dtype, direction): 0 = built-in default. Set by the autotuner.
 int g_variant[2][2][17];
 
-// Built-in choice: the two-stage tiled kernel for decompositions at N = 13, 14 (measured
-// faster there on GB300), else single-pass units of 8192 (4096 below N = 7) elements.
-int default_variant(int N, bool compose) {
-  if (!compose && (N == 13 || N == 14)) return kVariantTiled8;
+// Built-in choice (measured on GB300): the two-stage tiled kernel for decompositions at
+// N = 13, 14 -- two groups of 16 elements per thread, except one group of 8 for complex64 at
+// N = 13 -- else single-pass units of 8192 (4096 below N = 7) elements.
+int default_variant(int N, bool c64, bool compose) {
+  if (!compose && N == 14) return kVariantTiled16;
+  if (!compose && N == 13) return c64 ? kVariantTiled8 : kVariantTiled16;
   return N >= 7 ? kVariantUnit13 : kVariantUnit12;
 }
 // The single-pass choice, for requests the tiled kernel cannot take.
@@ -73,7 +75,7 @@ bool xordiag_variant_supported(int variant, int N, bool compose) { return varian
 int xordiag_get_variant(int N, bool c64, bool compose) {
   if (N < 0 || N > 16) return 0;
   const int v = g_variant[c64][compose][N];
-  return v ? v : (xordiag_supported(N) ? default_variant(N, compose) : 0);
+  return v ? v : (xordiag_supported(N) ? default_variant(N, c64, compose) : 0);
 }
 
 void xordiag_set_variant(int N, bool c64, bool compose, int variant) {
