@@ -155,6 +155,10 @@ class PauliPlan:
         self._lib = _lib.load()
         self.Ns = [int(n) for n in Ns]
         self.dtype = dtype
+        if not threads_per_block:  # the autotuned CTA size on this GPU model, if measured
+            from . import autotune
+
+            threads_per_block = autotune.plan_threads(dtype)
         narr = (ctypes.c_int * len(self.Ns))(*self.Ns)
         h = ctypes.c_void_p()
         check(self._lib.pauli_plan_create(narr, len(self.Ns), _DTYPES[dtype], int(threads_per_block),
