@@ -192,6 +192,11 @@ int pauli_version(void);
 /* Test hook for the host error path: when nonzero, the next `count` launches report
  * PAULI_ERR_CUDA as if the launch had failed, without enqueueing anything. */
 void pauli_debug_fail_next_launches(int count);
+/* Test hook for the device timeout path of the tiled variants: the next tiled launch makes its
+ * producers wait (a few milliseconds, bounded) on a count that nothing raises; they give up,
+ * record PAULI_ERR_TIMEOUT for pauli_stream_status and end the launch early (its output is
+ * then not valid). */
+void pauli_debug_stall_next_tiled(void);
 
 #ifdef __cplusplus
 }

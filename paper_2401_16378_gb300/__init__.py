@@ -6,5 +6,6 @@ include/pauli.h); this package is the thin binding. ``workloads`` holds the seed
 inputs and imports nothing else from the package.
 """
 from .api import (PauliDecompose, PauliError, PauliPlan, coeffs_at, compose, debug_fail_next_launches,  # noqa: F401
-                  decompose, decompose_autograd, decompose_host, decompose_list, last_error, pauli_coeffs_at, pauli_compose, pauli_decompose,
-                  pauli_decompose_host, pauli_decompose_list, set_variant, get_variant, stream_status, version)
+                  debug_stall_next_tiled, decompose, decompose_autograd, decompose_host, decompose_list, get_variant,
+                  last_error, pauli_coeffs_at, pauli_compose, pauli_decompose, pauli_decompose_host,
+                  pauli_decompose_list, set_variant, stream_status, version)

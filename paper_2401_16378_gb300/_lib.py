@@ -42,6 +42,7 @@ SIGNATURES = {
     "pauli_last_error": (ctypes.c_char_p, []),
     "pauli_version": (_i, []),
     "pauli_debug_fail_next_launches": (None, [_i]),
+    "pauli_debug_stall_next_tiled": (None, []),
 }
 
 _lock = threading.Lock()

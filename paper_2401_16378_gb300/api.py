@@ -248,6 +248,11 @@ def debug_fail_next_launches(count: int) -> None:
     _lib.load().pauli_debug_fail_next_launches(int(count))
 
 
+def debug_stall_next_tiled() -> None:
+    """Test hook: the next tiled launch gives up on a bounded device wait (PAULI_ERR_TIMEOUT)."""
+    _lib.load().pauli_debug_stall_next_tiled()
+
+
 # short aliases
 decompose = pauli_decompose
 compose = pauli_compose

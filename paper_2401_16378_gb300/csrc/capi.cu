@@ -128,6 +128,8 @@ int pauli_version(void) { return 100; }
 
 void pauli_debug_fail_next_launches(int count) { g_fail_next.store(count > 0 ? count : 0); }
 
+void pauli_debug_stall_next_tiled(void) { pauli::tiled_debug_stall_next(); }
+
 int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int method, void* stream) {
   int st = check_pair(G, "G", N, count, dtype, out, "out");
   if (st) return st;

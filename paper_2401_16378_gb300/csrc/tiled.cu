@@ -1,6 +1,7 @@
 // tiled.cu -- host side of the two-stage tiled decomposition: the scratch workspace per
 // (device, stream), dispatch to the per-shape instantiations, and the status word.
 // The kernel and the algorithm are in tiled_impl.cuh.
+#include <atomic>
 #include <cstddef>
 #include <mutex>
 #include <vector>
@@ -99,6 +100,13 @@ cudaError_t tiled_tensor_map(CUtensorMap* map, const void* G, int N, int count, 
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+namespace {
+std::atomic<bool> g_stall_next{false};
+}  // namespace
+
+void tiled_debug_stall_next() { g_stall_next.store(true); }
+bool tiled_take_stall() { return g_stall_next.exchange(false); }
 
 bool tiled_supported(int N) { return N >= 12 && N <= 14; }
 

@@ -18,7 +18,8 @@ struct TiledCtrl {
   int counter;                  // next work item
   int s1_done[kTiledSlots];     // stage-1 tiles completed per slot (all generations)
   int s2_done[kTiledSlots];     // stage-2 items that have copied their slot's data (all generations)
-  int pad1[7];
+  int stall;                    // test hook: the producer's first wait waits on a count nothing raises
+  int pad1[6];
   uint32_t emax[kTiledSlots][64];  // per class of the slot's block: (generation + 1) << 11 | exponent
 };
 constexpr size_t kTiledCtrlBytes = 2048;  // control block, padded; the slots follow
@@ -29,5 +30,9 @@ bool tiled_supported(int N);
 cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st);
 // Status word of the workspace used on `st` (synchronises st); 0 when none exists.
 cudaError_t tiled_stream_status(cudaStream_t st, int* status);
+// Test hook: the next tiled launch (any stream) stalls its producers on a wait that nothing
+// satisfies; the bounded wait gives up and records PAULI_ERR_TIMEOUT.
+void tiled_debug_stall_next();
+bool tiled_take_stall();
 
 }  // namespace pauli

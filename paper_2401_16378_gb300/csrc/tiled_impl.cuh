@@ -77,6 +77,7 @@ constexpr int kTB = kUB - kCB;     // log2 rows per stage-1 tile
 constexpr int kBufs = 3;           // shared-memory ring depth
 constexpr int kPolls = 1 << 24;    // bound of every wait loop (each poll sleeps or blocks briefly)
 constexpr int kStatusTimeout = 8;  // PAULI_ERR_TIMEOUT
+constexpr int kStallPolls = 1 << 15;  // the test hook's wait: well under a second
 
 template <int N>
 struct Geo {
@@ -264,8 +265,14 @@ __device__ void producer(const CUtensorMap* map, int count, TiledCtrl* ws, Share
     if (use >= kBufs && !wait_phase(smem_addr(&sh.empty[buf]), ((use / kBufs) - 1) & 1, &ws->status))
       break;  // the consumers never released the buffer: they give up on their own wait
     bool ok = true;
+    if (use == 0 && ws->stall) {  // test hook: wait (briefly) for a count nothing raises
+      int i = 0;
+      for (; i < kStallPolls && ld_acquire(&ws->stall) != 0x7FFFFFFF; ++i) __nanosleep(128);
+      atomicExch(&ws->status, kStatusTimeout);
+      ok = false;
+    }
     const int s = done ? 0 : it.b % GE::NS, gen = done ? 0 : it.b / GE::NS;
-    if (!done) {  // dependencies: the slot must be free (stage 1) or complete (stage 2)
+    if (!done && ok) {  // dependencies: the slot must be free (stage 1) or complete (stage 2)
       if (it.s1) {
         if (gen > 0) ok = wait_count(&ws->s2_done[s], GE::n2 * gen, &ws->status);
       } else {
@@ -664,6 +671,10 @@ cudaError_t launch_tiled_t(const void* G, int count, void* out, cudaStream_t st)
   e = cudaMemsetAsync(reinterpret_cast<char*>(ws) + offsetof(TiledCtrl, counter), 0,
                       sizeof(TiledCtrl) - offsetof(TiledCtrl, counter), st);
   if (e != cudaSuccess) return e;
+  if (tiled_take_stall()) {
+    e = cudaMemsetAsync(reinterpret_cast<char*>(ws) + offsetof(TiledCtrl, stall), 1, 1, st);
+    if (e != cudaSuccess) return e;
+  }
   kern<<<grid, TiledShape<RB>::kThreads, smem, st>>>(map, out, count, reinterpret_cast<TiledCtrl*>(ws));
   return cudaGetLastError();
 }

@@ -144,6 +144,28 @@ def test_tiled_c64_unaligned_matrix_takes_single_pass_path():
                  torch.complex64)
 
 
+def test_tiled_bounded_wait_reports_timeout_and_recovers():
+    """The stall hook makes the producers of the next tiled launch wait on a count that nothing
+    raises; the bounded wait gives up, the launch ends early, pauli_stream_status reports
+    PAULI_ERR_TIMEOUT once, and the next launch on the same stream is correct again."""
+    N = 12
+    G = workloads.gaussian_complex(N, 2800)
+    Gd = dev(G)
+    pg.set_variant(N, torch.complex128, "decompose", "tiled16")
+    try:
+        pg.debug_stall_next_tiled()
+        pg.decompose(Gd, method="xordiag")
+        with pytest.raises(pg.PauliError, match="TIMEOUT"):
+            pg.stream_status()
+        pg.stream_status()  # read once, then cleared
+        got = host(pg.decompose(Gd, method="xordiag"))
+        pg.stream_status()
+    finally:
+        pg.set_variant(N, torch.complex128, "decompose", "default")
+    idx = workloads.sample_indices(N, 2801, k=256)
+    assert_close(got[idx.astype(np.int64)], oracle.decompose_at(G, idx), np.max(np.abs(G)), torch.complex128)
+
+
 def test_tiled_variant_is_decompose_only():
     with pytest.raises(pg.PauliError, match="UNSUPPORTED"):
         pg.set_variant(14, torch.complex128, "compose", "tiled8")
