@@ -44,6 +44,9 @@ def parse():
                    help="XOR-diagonal launch shape of the timed step")
     p.add_argument("--profile", action="store_true",
                    help="only warm-up + timed kernel launches (for ncu); prints the step time")
+    p.add_argument("--forms-only", default="",
+                   help="comma list of secondary forms (n6, n12, c64, batched, adjoint) to run alone, "
+                        "without the timed step; prints their JSON")
     return p.parse_args()
 
 
@@ -250,6 +253,13 @@ def run_ours(args):
     import paper_2401_16378_gb300 as pg
     from paper_2401_16378_gb300 import workloads
 
+    if args.forms_only:
+        only = set(args.forms_only.split(","))
+        G14 = workloads.gaussian_complex(14, workloads.SEEDS["n14"]) if "c64" in only else None
+        forms = secondary_forms(pg, workloads, dev, torch.cuda.current_stream(dev), G14, only=only)
+        print(json.dumps({"forms": forms}), flush=True)
+        return
+
     N = args.n
     D = 1 << N
     ncoef = 4 ** N
@@ -373,7 +383,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def secondary_forms(pg, workloads, dev, stream, G14=None):
+def secondary_forms(pg, workloads, dev, stream, G14=None, only=None):
     """Plain, complex64, batched and adjoint forms on the same GPU, with their errors."""
     import torch
 
@@ -382,12 +392,31 @@ def secondary_forms(pg, workloads, dev, stream, G14=None):
     forms = {}
     reps = 5
 
+    def want(name):
+        return only is None or name in only
+
     def timed(fn, n=reps):
         fn()
         torch.cuda.synchronize(dev)
         return event_time(fn, n, stream)
 
-    # N=6 config: plain kernel, latency
+    if want("n6"):
+        n6_form(pg, workloads, dev, oracle, timed, forms)
+    if want("n12"):
+        n12_forms(pg, workloads, dev, oracle, timed, forms)
+    if want("c64") and G14 is not None:
+        c64_form(pg, workloads, dev, oracle, timed, forms, G14)
+    if want("batched"):
+        batched_forms(pg, workloads, dev, oracle, timed, forms)
+    if want("adjoint"):
+        adjoint_form(pg, workloads, dev, oracle, timed, forms)
+    return forms
+
+
+def n6_form(pg, workloads, dev, oracle, timed, forms):
+    """N=6 config: plain kernel, latency."""
+    import torch
+
     G6 = workloads.gaussian_complex(6, workloads.SEEDS["n6"])
     g6 = torch.from_numpy(G6).to(dev)
     o6 = torch.empty(4 ** 6, dtype=torch.complex128, device=dev)
@@ -395,7 +424,11 @@ def secondary_forms(pg, workloads, dev, stream, G14=None):
     err6 = float(np.max(np.abs(o6.cpu().numpy() - oracle.decompose_full(G6))) / np.max(np.abs(G6)))
     forms["n6_plain_c128"] = {"us_per_call": ms6 * 1e3, "coeffs_per_s": 4 ** 6 / (ms6 * 1e-3), "max_err_rel": err6}
 
-    # N=12 config: plain vs XOR-diagonal, general and Hermitian
+
+def n12_forms(pg, workloads, dev, oracle, timed, forms):
+    """N=12 config: plain vs XOR-diagonal, general and Hermitian."""
+    import torch
+
     N = 12
     for name, G in (("general", workloads.gaussian_complex(N, workloads.SEEDS["n12"])),
                     ("hermitian", workloads.hermitian_complex(N, workloads.SEEDS["n12_herm"]))):
@@ -414,24 +447,31 @@ def secondary_forms(pg, workloads, dev, stream, G14=None):
             forms[f"n12_{name}_{method}_c128"] = entry
         del g, o
 
-    # N=14 complex64 (TwoSum-compensated FP32): time and error against the FP64 oracle
-    if G14 is not None:
-        N = 14
-        G64 = G14.astype(np.complex64)
-        g = torch.from_numpy(G64).to(dev)
-        o = torch.empty(4 ** N, dtype=torch.complex64, device=dev)
-        ms = timed(lambda: pg.decompose(g, out=o, method="xordiag"), 10)
-        idx = workloads.sample_indices(N, workloads.SEEDS["n14_idx"])
-        want = oracle.decompose_at(G64.astype(np.complex128), idx)
-        got = o.cpu().numpy()[idx.astype(np.int64)].astype(np.complex128)
-        forms["n14_xordiag_c64"] = {"ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3),
-                                    "hbm_gbs_algorithmic": 2 * 4 ** N * 8 / (ms * 1e-3) / 1e9,
-                                    "max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(G64))),
-                                    "tolerance_rel": 2e-6}
-        del g, o, G64
 
-    # batched: 512 Hermitian matrices, N uniform in 3..10, one persistent graph-captured launch
-    # against 512 separate plain launches
+def c64_form(pg, workloads, dev, oracle, timed, forms, G14):
+    """N=14 complex64 (TwoSum-compensated FP32): time and error against the FP64 oracle."""
+    import torch
+
+    N = 14
+    G64 = G14.astype(np.complex64)
+    g = torch.from_numpy(G64).to(dev)
+    o = torch.empty(4 ** N, dtype=torch.complex64, device=dev)
+    ms = timed(lambda: pg.decompose(g, out=o, method="xordiag"), 10)
+    idx = workloads.sample_indices(N, workloads.SEEDS["n14_idx"])
+    want = oracle.decompose_at(G64.astype(np.complex128), idx)
+    got = o.cpu().numpy()[idx.astype(np.int64)].astype(np.complex128)
+    forms["n14_xordiag_c64"] = {"ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3),
+                                "hbm_gbs_algorithmic": 2 * 4 ** N * 8 / (ms * 1e-3) / 1e9,
+                                "max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(G64))),
+                                "tolerance_rel": 2e-6}
+    del g, o, G64
+
+
+def batched_forms(pg, workloads, dev, oracle, timed, forms):
+    """512 Hermitian matrices, N uniform in 3..10, one persistent graph-captured launch against
+    512 separate plain launches."""
+    import torch
+
     mats, Ns = workloads.batched_hermitian(workloads.SEEDS["batched"], batch=512)
     Ns = [int(n) for n in Ns]
     ncoef = sum(4 ** n for n in Ns)
@@ -463,36 +503,57 @@ def secondary_forms(pg, workloads, dev, stream, G14=None):
             "sample": "8 seeded coefficients per matrix vs the oracle"}
         del Gd, outs
 
-    # adjoint: 64 matrices at N=10, loss = sum_n w_n |c_n|^2, forward + backward
+
+def adjoint_form(pg, workloads, dev, oracle, timed, forms):
+    """64 matrices at N=10, loss = sum_n w_n |c_n|^2, forward + backward."""
+    import torch
+
     N, B = 10, 64
     A = workloads.adjoint_inputs(workloads.SEEDS["adjoint"], batch=B, N=N)
-    w = torch.from_numpy(workloads.adjoint_weights(workloads.SEEDS["adjoint_w"], N)).to(dev)
+    w_np = workloads.adjoint_weights(workloads.SEEDS["adjoint_w"], N)
+    w = torch.from_numpy(w_np).to(dev)
     Gt = torch.from_numpy(A).to(dev).requires_grad_(True)
 
-    def fwd_bwd(method):
+    def fwd_bwd(method, fused=True):
         Gt.grad = None
         c = pg.decompose_autograd(Gt, method=method)
-        loss = (w * c.abs() ** 2).sum()
+        loss = pg.weighted_norm_autograd(c, w) if fused else (w * c.abs() ** 2).sum()
         loss.backward()
-        return c
+        return c, loss
 
     ms_x = timed(lambda: fwd_bwd("xordiag"), 10)
-    c = fwd_bwd("xordiag").detach()
+    ms_t = timed(lambda: fwd_bwd("xordiag", fused=False), 3)
+    c, loss = fwd_bwd("xordiag")
     torch.cuda.synchronize(dev)
+    ch = c.detach().cpu().numpy()
+    want_loss = sum(oracle.weighted_norm(ch[k], w_np) for k in range(B))
     D = 1 << N
     rows = np.arange(0, D, 7)
     cols = (rows * 5 + 3) % D
-    c0 = c[0].cpu().numpy()
-    want = oracle.compose_at(2 * w.cpu().numpy() * c0, rows, cols) * 2.0 ** -N
+    want = oracle.compose_at(oracle.weighted_norm_grad(ch[0], w_np), rows, cols) * 2.0 ** -N
     got = Gt.grad[0].cpu().numpy()[rows, cols]
     ms_p = timed(lambda: fwd_bwd("plain"), 1)
+    # the four kernels of one step, each timed alone on the same buffers
+    Gd = Gt.detach()
+    cb = torch.empty_like(c)
+    lb = torch.empty((), dtype=torch.float64, device=dev)
+    gb = torch.empty_like(c)
+    Ob = torch.empty_like(Gd)
+    parts = {"decompose_ms": timed(lambda: pg.decompose(Gd, out=cb), 10),
+             "weighted_norm_ms": timed(lambda: pg.weighted_norm(cb, w, out=lb), 10),
+             "weighted_norm_grad_ms": timed(lambda: pg.weighted_norm_grad(cb, w, out=gb), 10),
+             "compose_ms": timed(lambda: pg.compose(gb, out=Ob, scale_exp=-N), 10)}
+    del cb, gb, Ob
     forms["adjoint64_n10_c128"] = {
         "fwd_bwd_ms": ms_x, "matrices_per_s": B / (ms_x * 1e-3), "coeffs_per_s": B * 4 ** N / (ms_x * 1e-3),
+        "calls": "decompose_autograd + weighted_norm_autograd (decompose, norm, norm_grad, compose kernels)",
+        "torch_elementwise_loss_fwd_bwd_ms": ms_t, "kernels_alone": parts,
         "plain_forward_fwd_bwd_ms": ms_p, "speedup_vs_plain": ms_p / ms_x,
+        "loss_err_rel": abs(float(loss.detach().cpu()) - want_loss) / want_loss,
         "grad_max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(want))),
-        "sample": "gradient of matrix 0 at 147 entries vs the oracle's compose of 2 w c"}
+        "sample": "loss vs the oracle's norm of the 64 coefficient vectors; gradient of matrix 0 at 147 "
+                  "entries vs the oracle's 2^-N compose of 2 w c"}
     del Gt, A
-    return forms
 
 
 def main():

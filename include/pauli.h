@@ -80,6 +80,29 @@ int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int m
  * 2^-N compose(grad_c), because every P_n is Hermitian). */
 int pauli_compose(const void* c, int N, int count, int dtype, void* G_out, int scale_exp, void* stream);
 
+/* Weighted norm of `count` coefficient vectors, a real loss of the decomposition:
+ *   *loss = sum_{k < count} sum_{n < 4^N} w_n |c[k * 4^N + n]|^2.
+ * With w = 1 and c = decompose(G) it equals 2^-N ||G||_F^2, since Tr(P_m P_n) = 2^N [m = n]
+ * (the Pauli tensors of Sec. 2 are Hermitian, unitary and trace-orthogonal).
+ *   c: device, count * 4^N complex values of dtype. w: device, 4^N reals -- double for
+ *   PAULI_C128, float for PAULI_C64. loss: device, one real of that type, overwritten.
+ * FP64 accumulation for PAULI_C128; compensated FP32 per thread and FP64 across threads for
+ * PAULI_C64. The summation order is fixed, so repeated calls give identical bits. Uses an
+ * 8 KiB device workspace per (device, stream), allocated with cudaMalloc at the first call
+ * on that pair and kept: make the first call before capturing the stream in a CUDA graph.
+ * loss must not overlap c or w (PAULI_ERR_ALIAS). */
+int pauli_weighted_norm(const void* c, int N, int count, int dtype, const void* w, void* loss, void* stream);
+
+/* Gradient of pauli_weighted_norm's loss with respect to c, in PyTorch's convention for a
+ * real function of complex inputs (dL/dRe c + i dL/dIm c), times the incoming gradient g:
+ *   grad_c[k * 4^N + n] = 2 g w_n c[k * 4^N + n].
+ * g: device pointer to one real of the loss's type, or NULL for g = 1. grad_c: device, same
+ * size and dtype as c; grad_c == c (in place) is allowed, any other overlap of grad_c with c,
+ * w or g is PAULI_ERR_ALIAS. Chained with pauli_compose(grad_c, scale_exp = -N) it gives the
+ * gradient of the loss with respect to G. Allocates nothing. */
+int pauli_weighted_norm_grad(const void* c, int N, int count, int dtype, const void* w, const void* g,
+                             void* grad_c, void* stream);
+
 /* Coefficients for a caller-chosen list of indices: out[q] = c_{idx[q]} for q < k, each by
  * the per-coefficient sum of Eq. (13) in O(2^N) work and no scratch memory -- the use the
  * paper's fixed-memory property is for (abstract; Sec. 3). idx is a device array of k

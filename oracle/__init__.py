@@ -10,6 +10,8 @@ Two independent formulations, both plain and slow:
   Neumaier-compensated FP64 sums, OpenMP over the requested outputs.
 * ``kron``: explicit Pauli tensors built by Kronecker products of the matrices of Eq. (3),
   and the trace of Eq. (4), in NumPy (used for N <= 4).
+* ``weighted_norm`` / ``weighted_norm_grad``: the real loss sum_n w_n |c_n|^2 of the adjoint
+  workload and its gradient 2 w c, by their definitions, in NumPy.
 
 Precision: FP64. A complex64 input is upcast exactly to complex128 before the call, so the
 oracle value for a complex64 input is the exact-input FP64 result.
@@ -17,6 +19,7 @@ oracle value for a complex64 input is the exact-input FP64 result.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -139,3 +142,27 @@ def decompose_grad(grad_c: np.ndarray, threads: int = 0) -> np.ndarray:
     grad_c = np.asarray(grad_c).ravel()
     N = (grad_c.size.bit_length() - 1) // 2
     return compose_full(grad_c, threads) * (2.0 ** -N)
+
+
+def weighted_norm(c: np.ndarray, w: np.ndarray) -> float:
+    """sum_k sum_n w_n |c_{k,n}|^2 for coefficient vectors along the last axis of c.
+
+    The real loss of the adjoint workload. Each term in FP64 from the exactly upcast input,
+    the terms added with math.fsum (correctly rounded sum of the rounded terms).
+    """
+    c = _as_c128(c)
+    w = np.asarray(w, dtype=np.float64)
+    if c.shape[-1] != w.size:
+        raise ValueError("w must hold one weight per coefficient index")
+    terms = w * (c.real * c.real + c.imag * c.imag)
+    return math.fsum(terms.ravel().tolist())
+
+
+def weighted_norm_grad(c: np.ndarray, w: np.ndarray, g: float = 1.0) -> np.ndarray:
+    """g times the gradient of weighted_norm in torch's convention for complex inputs:
+    dL/dRe c + i dL/dIm c = 2 w_n c_{k,n}, in FP64."""
+    c = _as_c128(c)
+    w = np.asarray(w, dtype=np.float64)
+    if c.shape[-1] != w.size:
+        raise ValueError("w must hold one weight per coefficient index")
+    return (2.0 * g * w) * c

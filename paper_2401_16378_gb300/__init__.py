@@ -5,7 +5,8 @@ The computation lives in libpauli.so (hand-written CUDA for sm_103a, C ABI in
 include/pauli.h); this package is the thin binding. ``workloads`` holds the seeded synthetic
 inputs and imports nothing else from the package.
 """
-from .api import (PauliDecompose, PauliError, PauliPlan, coeffs_at, compose, debug_fail_next_launches,  # noqa: F401
-                  debug_stall_next_tiled, decompose, decompose_autograd, decompose_host, decompose_list, get_variant,
-                  last_error, pauli_coeffs_at, pauli_compose, pauli_decompose, pauli_decompose_host,
-                  pauli_decompose_list, set_variant, stream_status, version)
+from .api import (PauliDecompose, PauliError, PauliPlan, PauliWeightedNorm, coeffs_at, compose,  # noqa: F401
+                  debug_fail_next_launches, debug_stall_next_tiled, decompose, decompose_autograd, decompose_host,
+                  decompose_list, get_variant, last_error, pauli_coeffs_at, pauli_compose, pauli_decompose,
+                  pauli_decompose_host, pauli_decompose_list, pauli_weighted_norm, pauli_weighted_norm_grad,
+                  set_variant, stream_status, version, weighted_norm, weighted_norm_autograd, weighted_norm_grad)

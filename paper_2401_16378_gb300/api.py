@@ -90,6 +90,54 @@ def pauli_compose(c: torch.Tensor, out: torch.Tensor | None = None, scale_exp: i
     return out
 
 
+_REAL = {torch.complex64: torch.float32, torch.complex128: torch.float64}
+
+
+def _weights(c: torch.Tensor, w: torch.Tensor, N: int) -> torch.Tensor:
+    _device_tensor(w, "w")
+    if w.dtype != _REAL[c.dtype] or w.numel() != 4 ** N:
+        raise ValueError(f"w must hold 4^N values of {_REAL[c.dtype]}")
+    return w
+
+
+def pauli_weighted_norm(c: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    """sum over the batch and n of w_n |c_n|^2 for a (..., 4^N) CUDA tensor; a 0-dim real tensor."""
+    _device_tensor(c, "c")
+    N = _qubits_of_coeffs(c)
+    _weights(c, w, N)
+    if out is None:
+        out = torch.empty((), dtype=_REAL[c.dtype], device=c.device)
+    _device_tensor(out, "out")
+    if out.dtype != _REAL[c.dtype] or out.numel() != 1:
+        raise ValueError("out must be one real of c's precision")
+    check(_lib.load().pauli_weighted_norm(c.data_ptr(), N, c.numel() // 4 ** N, _dtype(c), w.data_ptr(),
+                                          out.data_ptr(), _stream(stream)))
+    return out
+
+
+def pauli_weighted_norm_grad(c: torch.Tensor, w: torch.Tensor, g: torch.Tensor | None = None,
+                             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """2 g w_n c_n (g a one-element real CUDA tensor, or None for 1); out may be c itself."""
+    _device_tensor(c, "c")
+    N = _qubits_of_coeffs(c)
+    _weights(c, w, N)
+    gp = None
+    if g is not None:
+        _device_tensor(g, "g")
+        if g.dtype != _REAL[c.dtype] or g.numel() != 1:
+            raise ValueError("g must be one real of c's precision")
+        gp = g.data_ptr()
+    if out is None:
+        out = torch.empty_like(c)
+    _device_tensor(out, "out")
+    if out.dtype != c.dtype or out.numel() != c.numel():
+        raise ValueError("out must match c in dtype and number of elements")
+    check(_lib.load().pauli_weighted_norm_grad(c.data_ptr(), N, c.numel() // 4 ** N, _dtype(c), w.data_ptr(), gp,
+                                               out.data_ptr(), _stream(stream)))
+    return out
+
+
 def pauli_coeffs_at(G: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """c_n for the listed n (a CUDA int64/uint64 tensor), O(2^N) each, no scratch memory."""
     _device_tensor(G, "G")
@@ -216,6 +264,25 @@ def decompose_autograd(G: torch.Tensor, method="auto") -> torch.Tensor:
     return PauliDecompose.apply(G, method)
 
 
+class PauliWeightedNorm(torch.autograd.Function):
+    """L = sum w_n |c_n|^2 over the batch, with the hand-written gradient 2 g w c (w is constant)."""
+
+    @staticmethod
+    def forward(ctx, c: torch.Tensor, w: torch.Tensor):
+        c = c.contiguous()
+        ctx.save_for_backward(c, w)
+        return pauli_weighted_norm(c, w)
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        c, w = ctx.saved_tensors
+        return pauli_weighted_norm_grad(c, w, g.contiguous()), None
+
+
+def weighted_norm_autograd(c: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
+    return PauliWeightedNorm.apply(c, w)
+
+
 VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4, "tiled8": 5,
             "tiled16": 6}
 
@@ -259,3 +326,5 @@ compose = pauli_compose
 coeffs_at = pauli_coeffs_at
 decompose_list = pauli_decompose_list
 decompose_host = pauli_decompose_host
+weighted_norm = pauli_weighted_norm
+weighted_norm_grad = pauli_weighted_norm_grad

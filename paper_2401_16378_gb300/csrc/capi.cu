@@ -149,6 +149,56 @@ int pauli_compose(const void* c, int N, int count, int dtype, void* G_out, int s
   return PAULI_OK;
 }
 
+int pauli_weighted_norm(const void* c, int N, int count, int dtype, const void* w, void* loss, void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (count < 1) return fail(PAULI_ERR_ARG, "count = %d must be >= 1", count);
+  if (!c) return fail(PAULI_ERR_NULL, "c is NULL");
+  if (!w) return fail(PAULI_ERR_NULL, "w is NULL");
+  if (!loss) return fail(PAULI_ERR_NULL, "loss is NULL");
+  const size_t es = elem_bytes(dtype), rs = es / 2;
+  if ((st = check_aligned(c, es, "c"))) return st;
+  if ((st = check_aligned(w, rs, "w"))) return st;
+  if ((st = check_aligned(loss, rs, "loss"))) return st;
+  const size_t per = (size_t)1 << (2 * N);
+  if ((unsigned long long)count > (~0ull / es) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
+  if (overlaps(loss, rs, c, per * (size_t)count * es) || overlaps(loss, rs, w, per * rs))
+    return fail(PAULI_ERR_ALIAS, "loss overlaps c or w");
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e = pauli::launch_weighted_norm(c, N, count, dtype == PAULI_C64, w, loss, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_weighted_norm launch");
+  return PAULI_OK;
+}
+
+int pauli_weighted_norm_grad(const void* c, int N, int count, int dtype, const void* w, const void* g, void* grad_c,
+                             void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (count < 1) return fail(PAULI_ERR_ARG, "count = %d must be >= 1", count);
+  if (!c) return fail(PAULI_ERR_NULL, "c is NULL");
+  if (!w) return fail(PAULI_ERR_NULL, "w is NULL");
+  if (!grad_c) return fail(PAULI_ERR_NULL, "grad_c is NULL");
+  const size_t es = elem_bytes(dtype), rs = es / 2;
+  if ((st = check_aligned(c, es, "c"))) return st;
+  if ((st = check_aligned(grad_c, es, "grad_c"))) return st;
+  if ((st = check_aligned(w, rs, "w"))) return st;
+  if (g && (st = check_aligned(g, rs, "g"))) return st;
+  const size_t per = (size_t)1 << (2 * N);
+  if ((unsigned long long)count > (~0ull / es) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
+  const size_t bytes = per * (size_t)count * es;
+  if (grad_c != c && overlaps(grad_c, bytes, c, bytes))
+    return fail(PAULI_ERR_ALIAS, "grad_c overlaps c without being equal to it");
+  if (overlaps(grad_c, bytes, w, per * rs) || (g && overlaps(grad_c, bytes, g, rs)))
+    return fail(PAULI_ERR_ALIAS, "grad_c overlaps w or g");
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e =
+      pauli::launch_weighted_norm_grad(c, N, count, dtype == PAULI_C64, w, g, grad_c, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_weighted_norm_grad launch");
+  return PAULI_OK;
+}
+
 int pauli_set_variant(int N, int dtype, int op, int variant) {
   int st;
   if ((st = check_dtype(dtype))) return st;

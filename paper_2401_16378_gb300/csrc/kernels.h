@@ -29,4 +29,12 @@ void xordiag_set_variant(int N, bool c64, bool compose, int variant);
 cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, bool compose, int scale_exp, void* out,
                            cudaStream_t s, int variant = 0);
 
+// Weighted coefficient norm L = sum_k sum_n w_n |c_{k,n}|^2 (two launches, deterministic) and
+// its gradient grad_c = 2 g w_n c (one launch; grad_c may be c) (norm.cu). w and the outputs are
+// double for complex128, float for complex64; g is a device scalar or nullptr (g = 1).
+cudaError_t launch_weighted_norm(const void* c, int N, long long count, bool c64, const void* w, void* loss,
+                                 cudaStream_t s);
+cudaError_t launch_weighted_norm_grad(const void* c, int N, long long count, bool c64, const void* w, const void* g,
+                                      void* grad_c, cudaStream_t s);
+
 }  // namespace pauli

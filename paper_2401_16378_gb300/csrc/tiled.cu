@@ -1,14 +1,14 @@
-// tiled.cu -- host side of the two-stage tiled decomposition: the scratch workspace per
-// (device, stream), dispatch to the per-shape instantiations, and the status word.
+// tiled.cu -- host side of the two-stage tiled decomposition: its scratch workspace per
+// (device, stream), the tensor map, dispatch to the per-shape instantiations, and the status word.
 // The kernel and the algorithm are in tiled_impl.cuh.
 #include <atomic>
 #include <cstddef>
 #include <mutex>
-#include <vector>
 
 #include <cuda.h>
 
 #include "tiled.h"
+#include "workspace.h"
 
 namespace pauli {
 
@@ -17,49 +17,8 @@ cudaError_t tiled_launch_c128_r4(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_c64_r3(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_c64_r4(const void*, int, int, void*, cudaStream_t);
 
-namespace {
-
-// Workspace per (device, stream), grown on demand and kept for the life of the process.
-struct Workspace {
-  int dev;
-  cudaStream_t stream;
-  void* ptr;
-  size_t bytes;
-};
-std::mutex g_ws_mutex;
-std::vector<Workspace> g_ws;
-
-}  // namespace
-
 cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lock(g_ws_mutex);
-  for (Workspace& w : g_ws) {
-    if (w.dev != dev || w.stream != st) continue;
-    if (w.bytes < bytes) {
-      e = cudaFree(w.ptr);  // waits for the device, so no launch still uses it
-      if (e != cudaSuccess) return e;
-      w.ptr = nullptr;
-      w.bytes = 0;
-      e = cudaMalloc(&w.ptr, bytes);
-      if (e != cudaSuccess) return e;
-      w.bytes = bytes;
-      e = cudaMemsetAsync(w.ptr, 0, kTiledCtrlBytes, st);
-      if (e != cudaSuccess) return e;
-    }
-    *out = w.ptr;
-    return cudaSuccess;
-  }
-  void* p = nullptr;
-  e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(p, 0, kTiledCtrlBytes, st);
-  if (e != cudaSuccess) return e;
-  g_ws.push_back(Workspace{dev, st, p, bytes});
-  *out = p;
-  return cudaSuccess;
+  return stream_workspace(kWorkspaceTiled, st, bytes, kTiledCtrlBytes, out);
 }
 
 namespace {
@@ -119,16 +78,9 @@ cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, i
 
 cudaError_t tiled_stream_status(cudaStream_t st, int* status) {
   *status = 0;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  void* p = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_ws_mutex);
-    for (const Workspace& w : g_ws)
-      if (w.dev == dev && w.stream == st) p = w.ptr;
-  }
+  void* p = stream_workspace_find(kWorkspaceTiled, st);
   if (!p) return cudaSuccess;
+  cudaError_t e;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
   int* sp = reinterpret_cast<int*>(reinterpret_cast<char*>(p) + offsetof(TiledCtrl, status));
   if ((e = cudaMemcpyAsync(status, sp, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;

@@ -235,6 +235,45 @@ def test_gradient_of_weighted_norm_by_finite_differences():
         assert abs(grad[r, q] - (d_re + 1j * d_im)) < 1e-7
 
 
+@pytest.mark.parametrize("N", [1, 3])
+def test_weighted_norm_unit_weights_is_parseval(N):
+    """w = 1: sum_n |c_n|^2 = 2^-N ||G||_F^2, from Tr(P_m P_n) = 2^N [m = n] (Sec. 2)."""
+    G = _rand(N, 320 + N)
+    want = float(np.sum(np.abs(G) ** 2)) / 2 ** N
+    got = oracle.weighted_norm(oracle.decompose_full(G), np.ones(4 ** N))
+    assert abs(got - want) <= 1e-13 * want
+
+
+def test_weighted_norm_one_hot_and_batch():
+    N = 2
+    w = np.random.default_rng(330).uniform(size=4 ** N)
+    for k in (0, 5, 15):
+        c = np.zeros(4 ** N, dtype=np.complex128)
+        c[k] = 3 - 4j
+        assert oracle.weighted_norm(c, w) == 25.0 * w[k]
+    cb = workloads.gaussian_complex(N, 331).reshape(1, -1)[:, :16].repeat(3, axis=0) * np.array([[1], [2j], [-3]])
+    parts = [oracle.weighted_norm(row, w) for row in cb]
+    assert abs(oracle.weighted_norm(cb, w) - sum(parts)) <= 1e-14 * sum(parts)
+    assert abs(parts[1] - 4 * parts[0]) <= 1e-14 * parts[1] and abs(parts[2] - 9 * parts[0]) <= 1e-14 * parts[2]
+
+
+def test_weighted_norm_grad_by_finite_differences():
+    """g (dL/dRe c + i dL/dIm c) by central differences against weighted_norm_grad."""
+    N = 2
+    rng = np.random.default_rng(332)
+    c = rng.normal(size=4 ** N) + 1j * rng.normal(size=4 ** N)
+    w = rng.uniform(size=4 ** N)
+    g = 1.5
+    grad = oracle.weighted_norm_grad(c, w, g)
+    h = 1e-6
+    for k in (0, 7, 15):
+        e = np.zeros_like(c)
+        e[k] = 1
+        d_re = (oracle.weighted_norm(c + h * e, w) - oracle.weighted_norm(c - h * e, w)) / (2 * h)
+        d_im = (oracle.weighted_norm(c + 1j * h * e, w) - oracle.weighted_norm(c - 1j * h * e, w)) / (2 * h)
+        assert abs(grad[k] - g * (d_re + 1j * d_im)) < 1e-7
+
+
 def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.decompose_at(np.zeros((3, 3)), [0])
