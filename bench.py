@@ -445,6 +445,16 @@ def n12_forms(pg, workloads, dev, oracle, timed, forms):
             else:
                 entry["hbm_gbs_algorithmic"] = 2 * 4 ** N * 16 / (ms * 1e-3) / 1e9
             forms[f"n12_{name}_{method}_c128"] = entry
+        if name == "hermitian":
+            # real parts only (pauli_decompose_hermitian): 16 B read + 8 B written per coefficient
+            r = torch.empty(4 ** N, dtype=torch.float64, device=dev)
+            ms = timed(lambda: pg.decompose_hermitian(g, out=r), 20)
+            err = float(np.max(np.abs(r.cpu().numpy()[idx.astype(np.int64)] - want.real)) / np.max(np.abs(G)))
+            forms["n12_hermitian_xordiag_real_c128"] = {
+                "ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3), "max_err_rel": err,
+                "hbm_gbs_algorithmic": 4 ** N * (16 + 8) / (ms * 1e-3) / 1e9,
+                "max_abs_imag_dropped_rel": float(np.max(np.abs(want.imag)) / np.max(np.abs(G)))}
+            del r
         del g, o
 
 

@@ -74,6 +74,20 @@ typedef enum {
  * the first such call on a stream before capturing that stream into a CUDA graph. */
 int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int method, void* stream);
 
+/* Decomposition of Hermitian matrices: only the real parts are stored,
+ *   out_re[k * 4^N + n] = Re c_n of matrix k                                  Eq. (4), (13).
+ * Every P_n is Hermitian, so Tr(P_n G^H) is the conjugate of Tr(P_n G): for a Hermitian G every
+ * c_n is real and out_re holds all of it; for any G, out_re holds the coefficients of the
+ * Hermitian part (G + G^H) / 2. Halves the output bytes and the output conversion.
+ *   out_re: device, count * 4^N reals -- double for PAULI_C128, float for PAULI_C64, aligned
+ *   to 8 / 4 bytes; must not overlap G.
+ * Same methods, kernels and arithmetic as pauli_decompose, so each value is bit for bit the
+ * real part that pauli_decompose stores with the same launch shape. Launch shape: the tiled
+ * kernel where the decomposition's chosen variant is PAULI_VARIANT_TILED8/16 (N = 12..14;
+ * the same scratch buffer), else the single-pass kernel of 8192-element units with 16
+ * elements per thread (4096-element units at N = 6). */
+int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* out_re, int method, void* stream);
+
 /* Compose: G_out[k] = 2^scale_exp * sum_n c[k * 4^N + n] P_n                         Eq. (1).
  * scale_exp in [-64, 64] is an exact power-of-two factor; scale_exp = -N gives the adjoint
  * of pauli_decompose (the gradient of a real loss with respect to G is

@@ -6,7 +6,8 @@ include/pauli.h); this package is the thin binding. ``workloads`` holds the seed
 inputs and imports nothing else from the package.
 """
 from .api import (PauliDecompose, PauliError, PauliPlan, PauliWeightedNorm, coeffs_at, compose,  # noqa: F401
-                  debug_fail_next_launches, debug_stall_next_tiled, decompose, decompose_autograd, decompose_host,
-                  decompose_list, get_variant, last_error, pauli_coeffs_at, pauli_compose, pauli_decompose,
-                  pauli_decompose_host, pauli_decompose_list, pauli_weighted_norm, pauli_weighted_norm_grad,
-                  set_variant, stream_status, version, weighted_norm, weighted_norm_autograd, weighted_norm_grad)
+                  debug_fail_next_launches, debug_stall_next_tiled, decompose, decompose_autograd,
+                  decompose_hermitian, decompose_host, decompose_list, get_variant, last_error, pauli_coeffs_at,
+                  pauli_compose, pauli_decompose, pauli_decompose_hermitian, pauli_decompose_host,
+                  pauli_decompose_list, pauli_weighted_norm, pauli_weighted_norm_grad, set_variant, stream_status,
+                  version, weighted_norm, weighted_norm_autograd, weighted_norm_grad)

@@ -25,6 +25,7 @@ _ip = ctypes.POINTER(ctypes.c_int)
 SIGNATURES = {
     "pauli_decompose": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_compose": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
+    "pauli_decompose_hermitian": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_weighted_norm": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
     "pauli_weighted_norm_grad": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "pauli_coeffs_at": (_i, [_vp, _i, _i, _vp, _i64, _vp, _vp]),

@@ -75,6 +75,26 @@ def pauli_decompose(G: torch.Tensor, out: torch.Tensor | None = None, method="au
     return out
 
 
+def pauli_decompose_hermitian(G: torch.Tensor, out: torch.Tensor | None = None, method="auto",
+                              stream=None) -> torch.Tensor:
+    """Re c_n for a (..., 2^N, 2^N) complex CUDA tensor (all of c_n when G is Hermitian); returns
+    a real (..., 4^N) tensor of G's precision."""
+    _device_tensor(G, "G")
+    N = _qubits_of_matrix(G)
+    count = G.numel() // (4 ** N)
+    rdt = {torch.complex64: torch.float32, torch.complex128: torch.float64}.get(G.dtype)
+    if rdt is None:
+        raise TypeError(f"dtype {G.dtype} is not complex64 or complex128")
+    if out is None:
+        out = torch.empty(G.shape[:-2] + (4 ** N,), dtype=rdt, device=G.device)
+    _device_tensor(out, "out")
+    if out.dtype != rdt or out.numel() != G.numel():
+        raise ValueError("out must hold one real of G's precision per coefficient")
+    check(_lib.load().pauli_decompose_hermitian(G.data_ptr(), N, count, _dtype(G), out.data_ptr(), _method(method),
+                                                _stream(stream)))
+    return out
+
+
 def pauli_compose(c: torch.Tensor, out: torch.Tensor | None = None, scale_exp: int = 0, stream=None) -> torch.Tensor:
     """G = 2^scale_exp sum_n c_n P_n for a (..., 4^N) complex CUDA tensor; returns (..., 2^N, 2^N)."""
     _device_tensor(c, "c")
@@ -326,5 +346,6 @@ compose = pauli_compose
 coeffs_at = pauli_coeffs_at
 decompose_list = pauli_decompose_list
 decompose_host = pauli_decompose_host
+decompose_hermitian = pauli_decompose_hermitian
 weighted_norm = pauli_weighted_norm
 weighted_norm_grad = pauli_weighted_norm_grad

@@ -6,7 +6,9 @@
 namespace pauli {
 
 // Eq. (13) per coefficient, Gray-code order (plain.cu).
-cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s);
+// re: store only Re c_n, into count * 4^N reals.
+cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s,
+                                   bool re = false);
 cudaError_t launch_plain_compose(const void* c, int N, long long count, bool c64, int scale_exp, void* G,
                                 cudaStream_t s);
 cudaError_t launch_coeffs_at(const void* G, int N, bool c64, const uint64_t* idx, long long k, void* out,
@@ -28,6 +30,8 @@ int xordiag_get_variant(int N, bool c64, bool compose);
 void xordiag_set_variant(int N, bool c64, bool compose, int variant);
 cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, bool compose, int scale_exp, void* out,
                            cudaStream_t s, int variant = 0);
+// Decomposition storing only Re c_n, into count * 4^N reals (double / float).
+cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, void* out, cudaStream_t s);
 
 // Weighted coefficient norm L = sum_k sum_n w_n |c_{k,n}|^2 (two launches, deterministic) and
 // its gradient grad_c = 2 g w_n c (one launch; grad_c may be c) (norm.cu). w and the outputs are

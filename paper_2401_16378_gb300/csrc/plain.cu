@@ -66,7 +66,8 @@ struct AccC64 {
   __device__ __forceinline__ double total_im(int k) const { return (double)si[k] + (double)ei[k]; }
 };
 
-template <bool C64>
+// RE: store only Re c_n, into an array of reals (Hermitian decomposition).
+template <bool C64, bool RE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(const void* __restrict__ Gv, int N,
                                                                              long long count, void* __restrict__ outv) {
   using Acc = typename std::conditional<C64, AccC64, AccC128>::type;
@@ -154,10 +155,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
     double re = tr[k] * scale, im = ti[k] * scale;
     mul_i_pow(re, im, (uint32_t)__popc(x & z));
     const unsigned long long n = kmat * nco + pauli_index(x, z);
-    if (C64)
+    if (RE) {
+      if (C64)
+        reinterpret_cast<float*>(outv)[n] = (float)re;
+      else
+        reinterpret_cast<double*>(outv)[n] = re;
+    } else if (C64) {
       reinterpret_cast<float2*>(outv)[n] = make_float2((float)re, (float)im);
-    else
+    } else {
       reinterpret_cast<double2*>(outv)[n] = make_double2(re, im);
+    }
   }
 }
 
@@ -265,15 +272,15 @@ __global__ void __launch_bounds__(256) plain_compose_kernel(const void* __restri
 
 }  // namespace
 
-cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s) {
+cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s,
+                                   bool re) {
   const int lcw = N < 3 ? N : 3, lkz = lcw;
   const unsigned long long tiles = ((1ull << N) >> lcw) * ((1ull << N) >> lkz) * (unsigned long long)count;
   const unsigned long long blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-  if (c64)
-    plain_decompose_kernel<true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
-  else
-    plain_decompose_kernel<false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
+  auto kern = c64 ? (re ? plain_decompose_kernel<true, true> : plain_decompose_kernel<true, false>)
+                  : (re ? plain_decompose_kernel<false, true> : plain_decompose_kernel<false, false>);
+  kern<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
   return cudaGetLastError();
 }
 

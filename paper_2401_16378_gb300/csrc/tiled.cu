@@ -16,6 +16,10 @@ cudaError_t tiled_launch_c128_r3(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_c128_r4(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_c64_r3(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_c64_r4(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_re_c128_r3(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_re_c128_r4(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_re_c64_r3(const void*, int, int, void*, cudaStream_t);
+cudaError_t tiled_launch_re_c64_r4(const void*, int, int, void*, cudaStream_t);
 
 cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out) {
   return stream_workspace(kWorkspaceTiled, st, bytes, kTiledCtrlBytes, out);
@@ -69,11 +73,14 @@ bool tiled_take_stall() { return g_stall_next.exchange(false); }
 
 bool tiled_supported(int N) { return N >= 12 && N <= 14; }
 
-cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st) {
+cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st, bool re) {
   if (!tiled_supported(N)) return cudaErrorNotSupported;
-  if (rb == 3) return c64 ? tiled_launch_c64_r3(G, N, count, out, st) : tiled_launch_c128_r3(G, N, count, out, st);
-  if (rb == 4) return c64 ? tiled_launch_c64_r4(G, N, count, out, st) : tiled_launch_c128_r4(G, N, count, out, st);
-  return cudaErrorNotSupported;
+  using Fn = cudaError_t (*)(const void*, int, int, void*, cudaStream_t);
+  static const Fn table[2][2][2] = {  // [re][c64][rb == 4]
+      {{tiled_launch_c128_r3, tiled_launch_c128_r4}, {tiled_launch_c64_r3, tiled_launch_c64_r4}},
+      {{tiled_launch_re_c128_r3, tiled_launch_re_c128_r4}, {tiled_launch_re_c64_r3, tiled_launch_re_c64_r4}}};
+  if (rb != 3 && rb != 4) return cudaErrorNotSupported;
+  return table[re][c64][rb == 4](G, N, count, out, st);
 }
 
 cudaError_t tiled_stream_status(cudaStream_t st, int* status) {

@@ -27,7 +27,9 @@ static_assert(sizeof(TiledCtrl) <= kTiledCtrlBytes, "control block fits its padd
 
 bool tiled_supported(int N);
 // rb = log2 of the elements per consumer thread: 3 (512 consumer threads) or 4 (256).
-cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st);
+// re: store only the real parts, into an array of reals (Hermitian decomposition).
+cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st,
+                         bool re = false);
 // Status word of the workspace used on `st` (synchronises st); 0 when none exists.
 cudaError_t tiled_stream_status(cudaStream_t st, int* status);
 // Test hook: the next tiled launch (any stream) stalls its producers on a wait that nothing

@@ -39,6 +39,8 @@ cudaError_t xordiag_c128_decompose(int, int, const void*, long long, int, void*,
 cudaError_t xordiag_c128_compose(int, int, const void*, long long, int, void*, cudaStream_t);
 cudaError_t xordiag_c64_decompose(int, int, const void*, long long, int, void*, cudaStream_t);
 cudaError_t xordiag_c64_compose(int, int, const void*, long long, int, void*, cudaStream_t);
+cudaError_t xordiag_re_decompose_c128(int, const void*, long long, void*, cudaStream_t);
+cudaError_t xordiag_re_decompose_c64(int, const void*, long long, void*, cudaStream_t);
 
 namespace {
 
@@ -102,6 +104,17 @@ cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, boo
                    : xordiag_c64_decompose(variant, N, in, count, scale_exp, out, s);
   return compose ? xordiag_c128_compose(variant, N, in, count, scale_exp, out, s)
                  : xordiag_c128_decompose(variant, N, in, count, scale_exp, out, s);
+}
+
+// Real parts only: the tiled kernel where the decomposition's chosen shape is tiled (and the
+// batch and alignment allow it), else the single-pass 16-element-per-thread units.
+cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, void* out, cudaStream_t s) {
+  if (!xordiag_supported(N)) return cudaErrorNotSupported;
+  const int v = xordiag_get_variant(N, c64, false);
+  if ((v == kVariantTiled8 || v == kVariantTiled16) && tiled_supported(N) && count <= kTiledMaxCount &&
+      !(reinterpret_cast<uintptr_t>(in) & 15u))
+    return launch_tiled(in, N, (int)count, c64, out, v == kVariantTiled8 ? 3 : 4, s, true);
+  return c64 ? xordiag_re_decompose_c64(N, in, count, out, s) : xordiag_re_decompose_c128(N, in, count, out, s);
 }
 
 }  // namespace pauli

@@ -341,6 +341,46 @@ struct ArC64 {
   __device__ static __forceinline__ void align(Elem&, int) {}
 };
 
+// Real-part output: the arithmetic of Base, but only Re(v * i^k) is converted and stored,
+// into an array of reals (double or float) indexed like the complex output. For a Hermitian
+// G every c_n is real and this is all of it; for any G it is c_n((G + G^H) / 2).
+// Re(v i^k) = (-1)^[k in {1, 2}] (k odd ? Im v : Re v).
+template <class Base>
+struct ReOut;
+
+template <>
+struct ReOut<ArC128> : ArC128 {
+  __device__ static __forceinline__ double re_value(const Elem& a, const Conv& cv, uint32_t k) {
+    return from_fixed((k & 1u) ? a.im : a.re, cv, (k << 31) ^ (k << 30));
+  }
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    reinterpret_cast<double*>(p)[i] = re_value(a, cv, k);
+  }
+  __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
+                                                    uint32_t k, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(reinterpret_cast<double*>(p) + i),
+                 "d"(re_value(a, cv, k)), "l"(pol)
+                 : "memory");
+  }
+};
+
+template <>
+struct ReOut<ArC64> : ArC64 {
+  __device__ static __forceinline__ float re_value(const Elem& a, const Conv& cv, uint32_t k) {
+    const float v = (k & 1u) ? __fadd_rn(a.ih, a.il) : __fadd_rn(a.rh, a.rl);
+    return __fmul_rn(((k ^ (k >> 1)) & 1u) ? -v : v, cv.scale);
+  }
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    reinterpret_cast<float*>(p)[i] = re_value(a, cv, k);
+  }
+  __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
+                                                    uint32_t k, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(reinterpret_cast<float*>(p) + i),
+                 "f"(re_value(a, cv, k)), "l"(pol)
+                 : "memory");
+  }
+};
+
 // Butterflies over the low G register-index bits.
 template <class AR, int G, int E>
 __device__ __forceinline__ void wht_regs(typename AR::Elem (&v)[E]) {

@@ -90,6 +90,21 @@ def test_compose_rejects_bad_arguments(lib):
     assert lib.pauli_compose(P(A), 4, 1, 3, P(B), 0, None) == DTYPE
 
 
+def test_hermitian_and_norm_reject_bad_arguments(lib):
+    assert lib.pauli_decompose_hermitian(P(A), 4, 1, C128, None, 0, None) == NULL
+    assert lib.pauli_decompose_hermitian(P(A), 4, 1, C128, P(B + 4), 0, None) == ALIGN
+    assert lib.pauli_decompose_hermitian(P(A), 4, 1, C64, P(B + 2), 0, None) == ALIGN
+    assert lib.pauli_decompose_hermitian(P(A), 4, 1, C128, P(A + 8 * 255), 0, None) == ALIAS
+    assert lib.pauli_decompose_hermitian(P(A), 4, 0, C128, P(B), 0, None) == ARG
+    assert lib.pauli_decompose_hermitian(P(A), 3, 1, C128, P(B), 2, None) == UNSUP
+    assert lib.pauli_weighted_norm(P(A), 4, 1, C128, None, P(B), None) == NULL
+    assert lib.pauli_weighted_norm(P(A), 4, 1, C128, P(B), P(A + 8), None) == ALIAS  # loss inside c
+    assert lib.pauli_weighted_norm(P(A), 4, 1, C128, P(B + 4), P(B + 4096), None) == ALIGN
+    assert lib.pauli_weighted_norm_grad(P(A), 4, 1, C128, P(B), None, P(A + 16), None) == ALIAS
+    assert lib.pauli_weighted_norm_grad(P(A), 4, 1, C128, P(B), None, P(B + 16), None) == ALIAS  # over w
+    assert lib.pauli_weighted_norm_grad(P(A), 4, 1, C128, P(B), P(B + 4), P(B + 65536), None) == ALIGN
+
+
 def test_coeffs_at_rejects_bad_arguments(lib):
     assert lib.pauli_coeffs_at(P(A), 4, C128, P(B), 0, P(B + 4096), None) == OK  # k = 0: nothing to do
     assert lib.pauli_coeffs_at(P(A), 4, C128, P(B), -1, P(B + 4096), None) == ARG

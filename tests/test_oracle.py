@@ -274,6 +274,16 @@ def test_weighted_norm_grad_by_finite_differences():
         assert abs(grad[k] - g * (d_re + 1j * d_im)) < 1e-7
 
 
+@pytest.mark.parametrize("N", [1, 3])
+def test_real_part_is_the_hermitian_part(N):
+    """Re c_n(G) = c_n((G + G^H)/2): every P_n is Hermitian, so Tr(P_n G^H) = conj Tr(P_n G)
+    (the identity the real-part decomposition relies on)."""
+    G = _rand(N, 340 + N)
+    H = (G + G.conj().T) / 2
+    np.testing.assert_allclose(oracle.decompose_full(G).real, oracle.decompose_full(H).real, rtol=0, atol=1e-14)
+    assert np.max(np.abs(oracle.decompose_full(H).imag)) <= 1e-14
+
+
 def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.decompose_at(np.zeros((3, 3)), [0])
