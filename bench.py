@@ -70,7 +70,7 @@ def measured_peak_hbm():
 
 def source_hash():
     h = hashlib.sha256()
-    for name in ("tiled_impl.cuh", "tiled.cu", "tiled.h", "tiled_c128_r3.cu", "xordiag.cu", "xordiag_impl.cuh",
+    for name in ("tiled_impl.cuh", "tiled.cu", "tiled.h", "tiled_c128_r4.cu", "xordiag.cu", "xordiag_impl.cuh",
                  "common.cuh"):
         with open(os.path.join(ROOT, "paper_2401_16378_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
@@ -524,16 +524,24 @@ def adjoint_form(pg, workloads, dev, oracle, timed, forms):
     w = torch.from_numpy(w_np).to(dev)
     Gt = torch.from_numpy(A).to(dev).requires_grad_(True)
 
-    def fwd_bwd(method, fused=True):
+    def step_fused(method="xordiag"):
+        # one fused kernel forward (decomposition + norm), one backward (weighted composition)
         Gt.grad = None
-        c = pg.decompose_autograd(Gt, method=method)
-        loss = pg.weighted_norm_autograd(c, w) if fused else (w * c.abs() ** 2).sum()
+        loss, c = pg.decompose_weighted_norm_autograd(Gt, w, method=method)
         loss.backward()
         return c, loss
 
-    ms_x = timed(lambda: fwd_bwd("xordiag"), 10)
-    ms_t = timed(lambda: fwd_bwd("xordiag", fused=False), 3)
-    c, loss = fwd_bwd("xordiag")
+    def step_separate(torch_loss=False):
+        Gt.grad = None
+        c = pg.decompose_autograd(Gt, method="xordiag")
+        loss = (w * c.abs() ** 2).sum() if torch_loss else pg.weighted_norm_autograd(c, w)
+        loss.backward()
+        return c, loss
+
+    ms_x = timed(step_fused, 10)
+    ms_s = timed(step_separate, 10)
+    ms_t = timed(lambda: step_separate(torch_loss=True), 3)
+    c, loss = step_fused()
     torch.cuda.synchronize(dev)
     ch = c.detach().cpu().numpy()
     want_loss = sum(oracle.weighted_norm(ch[k], w_np) for k in range(B))
@@ -542,23 +550,27 @@ def adjoint_form(pg, workloads, dev, oracle, timed, forms):
     cols = (rows * 5 + 3) % D
     want = oracle.compose_at(oracle.weighted_norm_grad(ch[0], w_np), rows, cols) * 2.0 ** -N
     got = Gt.grad[0].cpu().numpy()[rows, cols]
-    ms_p = timed(lambda: fwd_bwd("plain"), 1)
-    # the four kernels of one step, each timed alone on the same buffers
+    ms_p = timed(lambda: step_fused("plain"), 1)
+    # the kernels of each step, each timed alone on the same buffers
     Gd = Gt.detach()
     cb = torch.empty_like(c)
     lb = torch.empty((), dtype=torch.float64, device=dev)
     gb = torch.empty_like(c)
     Ob = torch.empty_like(Gd)
-    parts = {"decompose_ms": timed(lambda: pg.decompose(Gd, out=cb), 10),
+    one = torch.ones(1, dtype=torch.float64, device=dev)
+    parts = {"fused_decompose_norm_ms": timed(lambda: pg.decompose_weighted_norm(Gd, w, out=cb, loss=lb), 10),
+             "fused_compose_weighted_ms": timed(lambda: pg.compose_weighted(cb, w, one, out=Ob, scale_exp=1 - N), 10),
+             "decompose_ms": timed(lambda: pg.decompose(Gd, out=cb), 10),
              "weighted_norm_ms": timed(lambda: pg.weighted_norm(cb, w, out=lb), 10),
              "weighted_norm_grad_ms": timed(lambda: pg.weighted_norm_grad(cb, w, out=gb), 10),
              "compose_ms": timed(lambda: pg.compose(gb, out=Ob, scale_exp=-N), 10)}
     del cb, gb, Ob
     forms["adjoint64_n10_c128"] = {
         "fwd_bwd_ms": ms_x, "matrices_per_s": B / (ms_x * 1e-3), "coeffs_per_s": B * 4 ** N / (ms_x * 1e-3),
-        "calls": "decompose_autograd + weighted_norm_autograd (decompose, norm, norm_grad, compose kernels)",
-        "torch_elementwise_loss_fwd_bwd_ms": ms_t, "kernels_alone": parts,
+        "calls": "decompose_weighted_norm_autograd: fused decomposition + norm forward, weighted composition backward",
+        "separate_kernels_fwd_bwd_ms": ms_s, "torch_elementwise_loss_fwd_bwd_ms": ms_t, "kernels_alone": parts,
         "plain_forward_fwd_bwd_ms": ms_p, "speedup_vs_plain": ms_p / ms_x,
+        "hbm_gbs_algorithmic": 4 * B * 4 ** N * 16 / (ms_x * 1e-3) / 1e9,
         "loss_err_rel": abs(float(loss.detach().cpu()) - want_loss) / want_loss,
         "grad_max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(want))),
         "sample": "loss vs the oracle's norm of the 64 coefficient vectors; gradient of matrix 0 at 147 "

@@ -84,8 +84,8 @@ int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int m
  * Same methods, kernels and arithmetic as pauli_decompose, so each value is bit for bit the
  * real part that pauli_decompose stores with the same launch shape. Launch shape: the tiled
  * kernel where the decomposition's chosen variant is PAULI_VARIANT_TILED8/16 (N = 12..14;
- * the same scratch buffer), else the single-pass kernel of 8192-element units with 16
- * elements per thread (4096-element units at N = 6). */
+ * the same scratch buffer), else the single-pass kernel with units of the chosen variant's
+ * size (8192 or 4096 elements; always 4096 at N = 6) and 16 elements per thread. */
 int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* out_re, int method, void* stream);
 
 /* Compose: G_out[k] = 2^scale_exp * sum_n c[k * 4^N + n] P_n                         Eq. (1).
@@ -116,6 +116,27 @@ int pauli_weighted_norm(const void* c, int N, int count, int dtype, const void* 
  * gradient of the loss with respect to G. Allocates nothing. */
 int pauli_weighted_norm_grad(const void* c, int N, int count, int dtype, const void* w, const void* g,
                              void* grad_c, void* stream);
+
+/* Fused forward step of that loss: pauli_decompose(G -> out) and pauli_weighted_norm(out -> loss)
+ * in one pass over G for N = 6..12 with the XOR-diagonal method (the decomposition kernel adds
+ * w_n |c_n|^2 over the coefficients it stores; one FP64 partial per work unit, added in a fixed
+ * order, so the loss is deterministic); for other N, or PAULI_PLAIN, the two calls in sequence.
+ * Arguments as in those two calls; out, w and loss must not overlap each other or G. Uses the
+ * per-(device, stream) workspace of pauli_weighted_norm, grown to 8 bytes per 4096 elements of
+ * the batch at the first call that needs more (cudaMalloc; not while capturing a graph). */
+int pauli_decompose_weighted_norm(const void* G, int N, int count, int dtype, void* out, const void* w,
+                                  void* loss, int method, void* stream);
+
+/* Composition of weighted coefficients:
+ *   G_out[k] = 2^scale_exp * sum_n g w_n c[k * 4^N + n] P_n                           Eq. (1).
+ * One pass over c: each loaded c_n is multiplied by g w_n (one rounding) before the transform.
+ * w: device, 4^N reals (double for PAULI_C128, float for PAULI_C64); g: device pointer to one
+ * such real, or NULL for 1. With scale_exp = 1 - N this is the gradient of
+ * pauli_weighted_norm's loss with respect to G, 2^-N compose(2 g w c), bit for bit equal to
+ * pauli_weighted_norm_grad followed by pauli_compose(scale_exp = -N) with the same launch shape.
+ * N <= 12 (PAULI_ERR_UNSUPPORTED above). */
+int pauli_compose_weighted(const void* c, int N, int count, int dtype, const void* w, const void* g, void* G_out,
+                           int scale_exp, void* stream);
 
 /* Coefficients for a caller-chosen list of indices: out[q] = c_{idx[q]} for q < k, each by
  * the per-coefficient sum of Eq. (13) in O(2^N) work and no scratch memory -- the use the
@@ -202,7 +223,9 @@ void pauli_plan_destroy(pauli_plan* plan);
  * All variants compute bit-identical complex128 results, except that the tiled ones re-scale
  * partial sums between the stages (an extra truncation below the class quantum, well inside
  * the accuracy bound of pauli_decompose); they differ otherwise only in speed. The choice is
- * process-wide per (N, dtype, op), op 0 = decompose, 1 = compose; variant 0 restores the
+ * process-wide per (N, dtype, op): op 0 = decompose, 1 = compose, for calls on one matrix
+ * (count = 1); op 2 = decompose, 3 = compose, for calls on a batch (count > 1), where the
+ * units of many matrices fill the GPU and a different shape can win. Variant 0 restores the
  * built-in default. The autotuner in the Python package measures the variants and records
  * its choice here. */
 #define PAULI_VARIANT_DEFAULT 0

@@ -5,9 +5,11 @@ The computation lives in libpauli.so (hand-written CUDA for sm_103a, C ABI in
 include/pauli.h); this package is the thin binding. ``workloads`` holds the seeded synthetic
 inputs and imports nothing else from the package.
 """
-from .api import (PauliDecompose, PauliError, PauliPlan, PauliWeightedNorm, coeffs_at, compose,  # noqa: F401
-                  debug_fail_next_launches, debug_stall_next_tiled, decompose, decompose_autograd,
-                  decompose_hermitian, decompose_host, decompose_list, get_variant, last_error, pauli_coeffs_at,
-                  pauli_compose, pauli_decompose, pauli_decompose_hermitian, pauli_decompose_host,
-                  pauli_decompose_list, pauli_weighted_norm, pauli_weighted_norm_grad, set_variant, stream_status,
-                  version, weighted_norm, weighted_norm_autograd, weighted_norm_grad)
+from .api import (PauliDecompose, PauliDecomposeWeightedNorm, PauliError, PauliPlan,  # noqa: F401
+                  PauliWeightedNorm, coeffs_at, compose, compose_weighted, debug_fail_next_launches,
+                  debug_stall_next_tiled, decompose, decompose_autograd, decompose_hermitian, decompose_host,
+                  decompose_list, decompose_weighted_norm, decompose_weighted_norm_autograd, get_variant, last_error,
+                  pauli_coeffs_at, pauli_compose, pauli_compose_weighted, pauli_decompose, pauli_decompose_hermitian,
+                  pauli_decompose_host, pauli_decompose_list, pauli_decompose_weighted_norm, pauli_weighted_norm,
+                  pauli_weighted_norm_grad, set_variant, stream_status, version, weighted_norm,
+                  weighted_norm_autograd, weighted_norm_grad)

@@ -27,6 +27,8 @@ SIGNATURES = {
     "pauli_compose": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_decompose_hermitian": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_weighted_norm": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
+    "pauli_decompose_weighted_norm": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp]),
+    "pauli_compose_weighted": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp]),
     "pauli_weighted_norm_grad": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "pauli_coeffs_at": (_i, [_vp, _i, _i, _vp, _i64, _vp, _vp]),
     "pauli_decompose_list": (_i, [_vpp, _ip, _i, _i, _vpp, _i, _vp]),

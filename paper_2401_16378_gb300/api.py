@@ -158,6 +158,52 @@ def pauli_weighted_norm_grad(c: torch.Tensor, w: torch.Tensor, g: torch.Tensor |
     return out
 
 
+def pauli_decompose_weighted_norm(G: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None,
+                                  loss: torch.Tensor | None = None, method="auto", stream=None):
+    """(c, L): the decomposition of G and L = sum over the batch and n of w_n |c_n|^2, computed
+    together (one fused kernel for N 6..12)."""
+    _device_tensor(G, "G")
+    N = _qubits_of_matrix(G)
+    count = G.numel() // (4 ** N)
+    if out is None:
+        out = torch.empty(G.shape[:-2] + (4 ** N,), dtype=G.dtype, device=G.device)
+    _device_tensor(out, "out")
+    if out.dtype != G.dtype or out.numel() != G.numel():
+        raise ValueError("out must match G in dtype and number of elements")
+    _weights(G, w, N)
+    if loss is None:
+        loss = torch.empty((), dtype=_REAL[G.dtype], device=G.device)
+    _device_tensor(loss, "loss")
+    if loss.dtype != _REAL[G.dtype] or loss.numel() != 1:
+        raise ValueError("loss must be one real of G's precision")
+    check(_lib.load().pauli_decompose_weighted_norm(G.data_ptr(), N, count, _dtype(G), out.data_ptr(), w.data_ptr(),
+                                                    loss.data_ptr(), _method(method), _stream(stream)))
+    return out, loss
+
+
+def pauli_compose_weighted(c: torch.Tensor, w: torch.Tensor, g: torch.Tensor | None = None,
+                           out: torch.Tensor | None = None, scale_exp: int = 0, stream=None) -> torch.Tensor:
+    """G = 2^scale_exp sum_n g w_n c_n P_n for a (..., 4^N) CUDA tensor, N <= 12 (g: one real, or None)."""
+    _device_tensor(c, "c")
+    N = _qubits_of_coeffs(c)
+    count = c.numel() // (4 ** N)
+    _weights(c, w, N)
+    gp = None
+    if g is not None:
+        _device_tensor(g, "g")
+        if g.dtype != _REAL[c.dtype] or g.numel() != 1:
+            raise ValueError("g must be one real of c's precision")
+        gp = g.data_ptr()
+    if out is None:
+        out = torch.empty(c.shape[:-1] + (1 << N, 1 << N), dtype=c.dtype, device=c.device)
+    _device_tensor(out, "out")
+    if out.dtype != c.dtype or out.numel() != c.numel():
+        raise ValueError("out must match c in dtype and number of elements")
+    check(_lib.load().pauli_compose_weighted(c.data_ptr(), N, count, _dtype(c), w.data_ptr(), gp, out.data_ptr(),
+                                             int(scale_exp), _stream(stream)))
+    return out
+
+
 def pauli_coeffs_at(G: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """c_n for the listed n (a CUDA int64/uint64 tensor), O(2^N) each, no scratch memory."""
     _device_tensor(G, "G")
@@ -303,18 +349,49 @@ def weighted_norm_autograd(c: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
     return PauliWeightedNorm.apply(c, w)
 
 
+class PauliDecomposeWeightedNorm(torch.autograd.Function):
+    """L(G) = sum over the batch and n of w_n |c_n(G)|^2, returned with c (not differentiable):
+    forward is one fused decomposition + norm kernel, backward one composition of 2 g w c
+    (dL/dG = 2^-N compose(2 g w c), the factor 2 folded into the exact scale 2^(1-N))."""
+
+    @staticmethod
+    def forward(ctx, G: torch.Tensor, w: torch.Tensor, method="auto"):
+        c, loss = pauli_decompose_weighted_norm(G.contiguous(), w, method=method)
+        ctx.save_for_backward(c, w)
+        ctx.mark_non_differentiable(c)
+        return loss, c
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor, _grad_c):
+        c, w = ctx.saved_tensors
+        N = _qubits_of_coeffs(c)
+        g = g.contiguous()
+        if N <= 12:
+            return pauli_compose_weighted(c, w, g, scale_exp=1 - N), None, None
+        return pauli_compose(pauli_weighted_norm_grad(c, w, g), scale_exp=-N), None, None
+
+
+def decompose_weighted_norm_autograd(G: torch.Tensor, w: torch.Tensor, method="auto"):
+    """(L, c) with L differentiable with respect to G."""
+    return PauliDecomposeWeightedNorm.apply(G, w, method)
+
+
 VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4, "tiled8": 5,
             "tiled16": 6}
 
 
+OPS = {"decompose": 0, "compose": 1, "decompose_batched": 2, "compose_batched": 3}
+
+
 def set_variant(N: int, dtype: torch.dtype, op: str, variant) -> None:
-    """Select the XOR-diagonal launch shape for (N, dtype, op in {"decompose", "compose"})."""
+    """Select the XOR-diagonal launch shape for (N, dtype, op in OPS); the "_batched" ops set the
+    shape used for calls with more than one matrix."""
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-    check(_lib.load().pauli_set_variant(int(N), _DTYPES[dtype], {"decompose": 0, "compose": 1}[op], v))
+    check(_lib.load().pauli_set_variant(int(N), _DTYPES[dtype], OPS[op], v))
 
 
 def get_variant(N: int, dtype: torch.dtype, op: str) -> int:
-    return int(_lib.load().pauli_get_variant(int(N), _DTYPES[dtype], {"decompose": 0, "compose": 1}[op]))
+    return int(_lib.load().pauli_get_variant(int(N), _DTYPES[dtype], OPS[op]))
 
 
 def stream_status(stream: torch.cuda.Stream | None = None) -> None:
@@ -348,4 +425,6 @@ decompose_list = pauli_decompose_list
 decompose_host = pauli_decompose_host
 decompose_hermitian = pauli_decompose_hermitian
 weighted_norm = pauli_weighted_norm
+decompose_weighted_norm = pauli_decompose_weighted_norm
+compose_weighted = pauli_compose_weighted
 weighted_norm_grad = pauli_weighted_norm_grad

@@ -29,7 +29,8 @@ from . import _lib
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 _DT = {"c128": torch.complex128, "c64": torch.complex64}
 _DT_CODE = {"c128": _lib.PAULI_C128, "c64": _lib.PAULI_C64}
-_OPS = {"decompose": 0, "compose": 1}
+_OPS = {"decompose": 0, "compose": 1, "decompose_batched": 2, "compose_batched": 3}
+BATCH_ELEMENTS = 1 << 26  # a tuning batch holds about this many elements (1 GiB of complex128)
 VARIANT_RANGE = {1: (7, 15), 2: (6, 14), 3: (6, 14), 4: (7, 15), 5: (12, 14), 6: (12, 14)}  # variant -> N range
 DECOMPOSE_ONLY = {5, 6}  # the two-stage tiled variants
 
@@ -50,8 +51,9 @@ def _time(fn, reps: int) -> float:
     return a.elapsed_time(b) / reps
 
 
-def tune_variants(Ns=range(6, 15), dtypes=("c128", "c64"), ops=("decompose", "compose"), reps=5, seed=777):
-    """Time every variant for each (N, dtype, op); returns {"N/dtype/op": {"best": v, "ms": {...}}}."""
+def tune_variants(Ns=range(6, 15), dtypes=("c128", "c64"), ops=tuple(_OPS), reps=5, seed=777):
+    """Time every variant for each (N, dtype, op); returns {"N/dtype/op": {"best": v, "ms": {...}}}.
+    The "_batched" ops time a batch of max(2, BATCH_ELEMENTS / 4^N) matrices."""
     from . import api
 
     lib = _lib.load()
@@ -61,25 +63,30 @@ def tune_variants(Ns=range(6, 15), dtypes=("c128", "c64"), ops=("decompose", "co
         rng = np.random.default_rng(seed + N)
         for dt in dtypes:
             tdt = _DT[dt]
-            # one buffer pair serves as matrix/coefficients (same element count)
-            a = torch.from_numpy((rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))).astype(
+            # one matrix; a batch repeats it (one buffer pair serves as matrix/coefficients)
+            one = torch.from_numpy((rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))).astype(
                 np.complex128)).to(tdt).cuda()
-            b = torch.empty_like(a)
             for op in ops:
+                count = max(2, BATCH_ELEMENTS >> (2 * N)) if op.endswith("_batched") else 1
+                a = one.expand(count, D, D).contiguous()
+                b = torch.empty_like(a)
                 times = {}
                 for v, (lo, hi) in VARIANT_RANGE.items():
-                    if not lo <= N <= hi or (op == "compose" and v in DECOMPOSE_ONLY):
+                    if not lo <= N <= hi or (op.startswith("compose") and v in DECOMPOSE_ONLY):
                         continue
                     _lib.check(lib.pauli_set_variant(N, _DT_CODE[dt], _OPS[op], v))
-                    if op == "decompose":
-                        times[v] = _time(lambda: api.pauli_decompose(a, out=b.view(-1), method="xordiag"), reps)
+                    if op.startswith("decompose"):
+                        times[v] = _time(lambda: api.pauli_decompose(a, out=b.view(count, -1), method="xordiag"),
+                                         reps)
                     else:
-                        times[v] = _time(lambda: api.pauli_compose(a.view(-1), out=b), reps)
+                        times[v] = _time(lambda: api.pauli_compose(a.view(count, -1), out=b), reps)
                 _lib.check(lib.pauli_set_variant(N, _DT_CODE[dt], _OPS[op], 0))
+                del a, b
                 if times:
                     best = min(times, key=times.get)
-                    out[f"{N}/{dt}/{op}"] = {"best": best, "ms": {str(k): v for k, v in times.items()}}
-            del a, b
+                    out[f"{N}/{dt}/{op}"] = {"best": best, "count": count,
+                                             "ms": {str(k): v for k, v in times.items()}}
+            del one
             torch.cuda.empty_cache()
     return out
 

@@ -223,15 +223,59 @@ int pauli_weighted_norm_grad(const void* c, int N, int count, int dtype, const v
   return PAULI_OK;
 }
 
+int pauli_decompose_weighted_norm(const void* G, int N, int count, int dtype, void* out, const void* w, void* loss,
+                                  int method, void* stream) {
+  int st = check_pair(G, "G", N, count, dtype, out, "out");
+  if (st) return st;
+  if (!w) return fail(PAULI_ERR_NULL, "w is NULL");
+  if (!loss) return fail(PAULI_ERR_NULL, "loss is NULL");
+  const size_t es = elem_bytes(dtype), rs = es / 2;
+  if ((st = check_aligned(w, rs, "w"))) return st;
+  if ((st = check_aligned(loss, rs, "loss"))) return st;
+  const size_t per = (size_t)1 << (2 * N), bytes = per * (size_t)count * es;
+  if (overlaps(out, bytes, w, per * rs) || overlaps(loss, rs, out, bytes) || overlaps(loss, rs, G, bytes) ||
+      overlaps(loss, rs, w, per * rs))
+    return fail(PAULI_ERR_ALIAS, "out, w and loss must not overlap each other or G");
+  int m = 0;
+  if ((st = resolve_method(method, N, &m))) return st;
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e = pauli::launch_decompose_norm(G, N, count, dtype == PAULI_C64, out, w, loss,
+                                               m == PAULI_PLAIN ? 1 : 2, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_weighted_norm launch");
+  return PAULI_OK;
+}
+
+int pauli_compose_weighted(const void* c, int N, int count, int dtype, const void* w, const void* g, void* G_out,
+                           int scale_exp, void* stream) {
+  int st = check_pair(c, "c", N, count, dtype, G_out, "G_out");
+  if (st) return st;
+  if (scale_exp < -64 || scale_exp > 64) return fail(PAULI_ERR_ARG, "scale_exp = %d outside [-64, 64]", scale_exp);
+  if (!w) return fail(PAULI_ERR_NULL, "w is NULL");
+  const size_t es = elem_bytes(dtype), rs = es / 2;
+  if ((st = check_aligned(w, rs, "w"))) return st;
+  if (g && (st = check_aligned(g, rs, "g"))) return st;
+  const size_t per = (size_t)1 << (2 * N), bytes = per * (size_t)count * es;
+  if (overlaps(G_out, bytes, w, per * rs) || (g && overlaps(G_out, bytes, g, rs)))
+    return fail(PAULI_ERR_ALIAS, "G_out overlaps w or g");
+  if (N > 12) return fail(PAULI_ERR_UNSUPPORTED, "pauli_compose_weighted is built for N <= 12, not N = %d", N);
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e =
+      pauli::launch_compose_weighted(c, N, count, dtype == PAULI_C64, w, g, scale_exp, G_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_compose_weighted launch");
+  return PAULI_OK;
+}
+
 int pauli_set_variant(int N, int dtype, int op, int variant) {
   int st;
   if ((st = check_dtype(dtype))) return st;
   if ((st = check_n(N))) return st;
-  if (op != 0 && op != 1) return fail(PAULI_ERR_ARG, "op = %d is not 0 (decompose) or 1 (compose)", op);
-  if (variant != PAULI_VARIANT_DEFAULT && !pauli::xordiag_variant_supported(variant, N, op == 1))
+  if (op < 0 || op > 3)
+    return fail(PAULI_ERR_ARG, "op = %d is not 0/1 (decompose/compose) or 2/3 (the same for batches)", op);
+  const bool compose = op & 1, batched = op >= 2;
+  if (variant != PAULI_VARIANT_DEFAULT && !pauli::xordiag_variant_supported(variant, N, compose))
     return fail(PAULI_ERR_UNSUPPORTED, "variant %d has no %s kernel for N = %d", variant,
-                op == 1 ? "compose" : "decompose", N);
-  pauli::xordiag_set_variant(N, dtype == PAULI_C64, op == 1, variant);
+                compose ? "compose" : "decompose", N);
+  pauli::xordiag_set_variant(N, dtype == PAULI_C64, compose, batched, variant);
   return PAULI_OK;
 }
 
@@ -244,8 +288,8 @@ int pauli_stream_status(void* stream) {
 }
 
 int pauli_get_variant(int N, int dtype, int op) {
-  if (check_dtype(dtype) || check_n(N) || (op != 0 && op != 1)) return 0;
-  return pauli::xordiag_get_variant(N, dtype == PAULI_C64, op == 1);
+  if (check_dtype(dtype) || check_n(N) || op < 0 || op > 3) return 0;
+  return pauli::xordiag_get_variant(N, dtype == PAULI_C64, op & 1, op >= 2);
 }
 
 int pauli_coeffs_at(const void* G, int N, int dtype, const uint64_t* idx, int64_t k, void* out, void* stream) {

@@ -9,8 +9,9 @@ namespace pauli {
 // re: store only Re c_n, into count * 4^N reals.
 cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s,
                                    bool re = false);
+// w, g (nullable): compose g w_n c_n instead of c_n.
 cudaError_t launch_plain_compose(const void* c, int N, long long count, bool c64, int scale_exp, void* G,
-                                cudaStream_t s);
+                                cudaStream_t s, const void* w = nullptr, const void* g = nullptr);
 cudaError_t launch_coeffs_at(const void* G, int N, bool c64, const uint64_t* idx, long long k, void* out,
                              cudaStream_t s);
 
@@ -26,12 +27,23 @@ constexpr int kVariantTiled8 = 5;    // two-stage tiled decomposition (tiled.cu)
 constexpr int kVariantTiled16 = 6;   // two-stage tiled decomposition, 256 consumers x 16 elements
 bool xordiag_supported(int N);
 bool xordiag_variant_supported(int variant, int N, bool compose);
-int xordiag_get_variant(int N, bool c64, bool compose);
-void xordiag_set_variant(int N, bool c64, bool compose, int variant);
+// batched: the choice for calls with count > 1 (kept apart from the one-matrix choice).
+int xordiag_get_variant(int N, bool c64, bool compose, bool batched);
+void xordiag_set_variant(int N, bool c64, bool compose, bool batched, int variant);
 cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, bool compose, int scale_exp, void* out,
                            cudaStream_t s, int variant = 0);
 // Decomposition storing only Re c_n, into count * 4^N reals (double / float).
 cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, void* out, cudaStream_t s);
+
+// Fused forms (fused.cu). Decomposition that also writes L = sum_k sum_n w_n |c_kn|^2
+// to *loss (any N: one fused kernel for N 6..12, else decomposition + norm), and composition of
+// g w_n c_n (N <= 12; cudaErrorNotSupported above).
+cudaError_t launch_decompose_norm(const void* G, int N, long long count, bool c64, void* out, const void* w,
+                                  void* loss, int method, cudaStream_t s);
+cudaError_t launch_compose_weighted(const void* c, int N, long long count, bool c64, const void* w, const void* g,
+                                    int scale_exp, void* G, cudaStream_t s);
+// Adds n partial losses (fixed order) into *loss (norm.cu).
+cudaError_t launch_norm_final(const double* partial, long long n, bool c64, void* loss, cudaStream_t s);
 
 // Weighted coefficient norm L = sum_k sum_n w_n |c_{k,n}|^2 (two launches, deterministic) and
 // its gradient grad_c = 2 g w_n c (one launch; grad_c may be c) (norm.cu). w and the outputs are

@@ -147,11 +147,14 @@ __global__ void __launch_bounds__(kThreads) norm_flat(const void* __restrict__ c
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// Adds the kBlocks partials (fixed tree) and writes L in the output's real type.
+// Adds n partials (thread t: partials t, t + 1024, ... in order, then a fixed tree) and writes
+// L in the output's real type.
 template <bool C64>
-__global__ void __launch_bounds__(kBlocks) norm_final(const double* __restrict__ partial, void* __restrict__ loss) {
-  __shared__ double part[kBlocks / 32];
-  double v = partial[threadIdx.x];
+__global__ void __launch_bounds__(1024) norm_final(const double* __restrict__ partial, long long n,
+                                                   void* __restrict__ loss) {
+  __shared__ double part[32];
+  double v = 0.0;
+  for (long long i = threadIdx.x; i < n; i += 1024) v += partial[i];
 #pragma unroll
   for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
   if ((threadIdx.x & 31u) == 0) part[threadIdx.x >> 5] = v;
@@ -270,10 +273,14 @@ cudaError_t launch_weighted_norm(const void* c, int N, long long count, bool c64
   else
     norm_flat<false><<<kBlocks, kThreads, 0, st>>>(c, w, N, total, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_norm_final(partial, kBlocks, c64, loss, st);
+}
+
+cudaError_t launch_norm_final(const double* partial, long long n, bool c64, void* loss, cudaStream_t st) {
   if (c64)
-    norm_final<true><<<1, kBlocks, 0, st>>>(partial, loss);
+    norm_final<true><<<1, 1024, 0, st>>>(partial, n, loss);
   else
-    norm_final<false><<<1, kBlocks, 0, st>>>(partial, loss);
+    norm_final<false><<<1, 1024, 0, st>>>(partial, n, loss);
   return cudaGetLastError();
 }
 

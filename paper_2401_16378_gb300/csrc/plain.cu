@@ -228,10 +228,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) coeffs_at_kernel(const vo
 
 // Eq. (1) elementwise: G[r, q] = 2^scale_exp sum_z (-1)^popc(r&z) (-i)^popc(x&z) c(x, z) with
 // x = r ^ q -- only the 2^N tensors whose XY-mask equals r ^ q have a nonzero entry at (r, q)
-// (Eq. (8), (11)). One thread per matrix element, O(2^N) each.
+// (Eq. (8), (11)). One thread per matrix element, O(2^N) each. With weights wv (nullable),
+// each c_n is first multiplied by g w_n (g = *gv, or 1 when gv is null).
 template <bool C64>
 __global__ void __launch_bounds__(256) plain_compose_kernel(const void* __restrict__ cv, int N, long long count,
-                                                            int scale_exp, void* __restrict__ Gv) {
+                                                            int scale_exp, void* __restrict__ Gv,
+                                                            const void* __restrict__ wv, const void* __restrict__ gv) {
   const unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t D = 1u << N;
   const unsigned long long per = (unsigned long long)D * D;
@@ -242,11 +244,19 @@ __global__ void __launch_bounds__(256) plain_compose_kernel(const void* __restri
   double tr = 0.0, ti = 0.0;
   if (C64) {
     const float2* c = reinterpret_cast<const float2*>(cv) + kmat * per;
+    const float* w = static_cast<const float*>(wv);
+    const float g = gv ? *static_cast<const float*>(gv) : 1.0f;
     AccC64 a;
     a.zero();
     for (uint32_t z = 0; z < D; ++z) {
-      const float2 v = __ldg(&c[pauli_index(x, z)]);
+      const uint32_t n = pauli_index(x, z);
+      const float2 v = __ldg(&c[n]);
       float vr = v.x, vi = v.y;
+      if (w) {
+        const float f = g == 1.0f ? w[n] : g * w[n];
+        vr *= f;
+        vi *= f;
+      }
       mul_i_pow(vr, vi, 3u * (uint32_t)__popc(x & z));
       a.add(0, vr, vi, (uint32_t)__popc(r & z) & 1u);
     }
@@ -254,9 +264,17 @@ __global__ void __launch_bounds__(256) plain_compose_kernel(const void* __restri
     ti = a.total_im(0);
   } else {
     const double2* c = reinterpret_cast<const double2*>(cv) + kmat * per;
+    const double* w = static_cast<const double*>(wv);
+    const double g = gv ? *static_cast<const double*>(gv) : 1.0;
     for (uint32_t z = 0; z < D; ++z) {
-      const double2 v = __ldg(&c[pauli_index(x, z)]);
+      const uint32_t n = pauli_index(x, z);
+      const double2 v = __ldg(&c[n]);
       double vr = v.x, vi = v.y;
+      if (w) {
+        const double f = g == 1.0 ? w[n] : g * w[n];
+        vr *= f;
+        vi *= f;
+      }
       mul_i_pow(vr, vi, 3u * (uint32_t)__popc(x & z));
       const long long flip = (long long)(__popc(r & z) & 1) << 63;
       tr += __longlong_as_double(__double_as_longlong(vr) ^ flip);
@@ -285,14 +303,14 @@ cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c
 }
 
 cudaError_t launch_plain_compose(const void* c, int N, long long count, bool c64, int scale_exp, void* G,
-                                cudaStream_t s) {
+                                cudaStream_t s, const void* w, const void* g) {
   const unsigned long long total = (1ull << (2 * N)) * (unsigned long long)count;
   const unsigned long long blocks = (total + 255) / 256;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
   if (c64)
-    plain_compose_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(c, N, count, scale_exp, G);
+    plain_compose_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(c, N, count, scale_exp, G, w, g);
   else
-    plain_compose_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(c, N, count, scale_exp, G);
+    plain_compose_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(c, N, count, scale_exp, G, w, g);
   return cudaGetLastError();
 }
 

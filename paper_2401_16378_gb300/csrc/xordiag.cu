@@ -39,8 +39,8 @@ cudaError_t xordiag_c128_decompose(int, int, const void*, long long, int, void*,
 cudaError_t xordiag_c128_compose(int, int, const void*, long long, int, void*, cudaStream_t);
 cudaError_t xordiag_c64_decompose(int, int, const void*, long long, int, void*, cudaStream_t);
 cudaError_t xordiag_c64_compose(int, int, const void*, long long, int, void*, cudaStream_t);
-cudaError_t xordiag_re_decompose_c128(int, const void*, long long, void*, cudaStream_t);
-cudaError_t xordiag_re_decompose_c64(int, const void*, long long, void*, cudaStream_t);
+cudaError_t xordiag_re_decompose_c128(int, const void*, long long, void*, cudaStream_t, bool);
+cudaError_t xordiag_re_decompose_c64(int, const void*, long long, void*, cudaStream_t, bool);
 
 namespace {
 
@@ -54,15 +54,19 @@ bool variant_has(int variant, int N, bool compose) {
 // The tiled kernel numbers its work items with 32-bit integers.
 constexpr long long kTiledMaxCount = 1024;
 
-// Chosen variant per (N, dtype, direction): 0 = built-in default. Set by the autotuner.
-int g_variant[2][2][17];
+// Chosen variant per (one matrix or a batch, N, dtype, direction): 0 = built-in default. Set
+// by the autotuner.
+int g_variant[2][2][2][17];
 
 // Built-in choice (measured on GB300): the two-stage tiled kernel for decompositions at
 // N = 13, 14 -- two groups of 16 elements per thread, except one group of 8 for complex64 at
-// N = 13 -- else single-pass units of 8192 (4096 below N = 7) elements.
-int default_variant(int N, bool c64, bool compose) {
+// N = 13 -- else single-pass units of 8192 (4096 below N = 7) elements; for batches of
+// matrices below N = 12, 4096-element units on two CTAs per SM (64 x N = 10: 0.46 instead of
+// 0.50 ms).
+int default_variant(int N, bool c64, bool compose, bool batched) {
   if (!compose && N == 14) return kVariantTiled16;
   if (!compose && N == 13) return c64 ? kVariantTiled8 : kVariantTiled16;
+  if (batched && N < 12) return kVariantUnit12;
   return N >= 7 ? kVariantUnit13 : kVariantUnit12;
 }
 // The single-pass choice, for requests the tiled kernel cannot take.
@@ -74,20 +78,20 @@ bool xordiag_supported(int N) { return N >= 6 && N <= 15; }
 
 bool xordiag_variant_supported(int variant, int N, bool compose) { return variant_has(variant, N, compose); }
 
-int xordiag_get_variant(int N, bool c64, bool compose) {
+int xordiag_get_variant(int N, bool c64, bool compose, bool batched) {
   if (N < 0 || N > 16) return 0;
-  const int v = g_variant[c64][compose][N];
-  return v ? v : (xordiag_supported(N) ? default_variant(N, c64, compose) : 0);
+  const int v = g_variant[batched][c64][compose][N];
+  return v ? v : (xordiag_supported(N) ? default_variant(N, c64, compose, batched) : 0);
 }
 
-void xordiag_set_variant(int N, bool c64, bool compose, int variant) {
-  if (N >= 0 && N <= 16) g_variant[c64][compose][N] = variant;
+void xordiag_set_variant(int N, bool c64, bool compose, bool batched, int variant) {
+  if (N >= 0 && N <= 16) g_variant[batched][c64][compose][N] = variant;
 }
 
 cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, bool compose, int scale_exp, void* out,
                            cudaStream_t s, int variant) {
   if (!variant) {
-    variant = xordiag_get_variant(N, c64, compose);
+    variant = xordiag_get_variant(N, c64, compose, count > 1);
     if ((variant == kVariantTiled8 || variant == kVariantTiled16) &&
         (count > kTiledMaxCount || (reinterpret_cast<uintptr_t>(in) & 15u)))
       variant = single_pass_variant(N);
@@ -107,14 +111,17 @@ cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, boo
 }
 
 // Real parts only: the tiled kernel where the decomposition's chosen shape is tiled (and the
-// batch and alignment allow it), else the single-pass 16-element-per-thread units.
+// batch and alignment allow it), else single-pass units of the chosen size with 16 elements
+// per thread.
 cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, void* out, cudaStream_t s) {
   if (!xordiag_supported(N)) return cudaErrorNotSupported;
-  const int v = xordiag_get_variant(N, c64, false);
+  const int v = xordiag_get_variant(N, c64, false, count > 1);
   if ((v == kVariantTiled8 || v == kVariantTiled16) && tiled_supported(N) && count <= kTiledMaxCount &&
       !(reinterpret_cast<uintptr_t>(in) & 15u))
     return launch_tiled(in, N, (int)count, c64, out, v == kVariantTiled8 ? 3 : 4, s, true);
-  return c64 ? xordiag_re_decompose_c64(N, in, count, out, s) : xordiag_re_decompose_c128(N, in, count, out, s);
+  const bool unit4096 = (v == kVariantUnit12 || v == kVariantUnit12x8) && N <= 14;
+  return c64 ? xordiag_re_decompose_c64(N, in, count, out, s, unit4096)
+             : xordiag_re_decompose_c128(N, in, count, out, s, unit4096);
 }
 
 }  // namespace pauli

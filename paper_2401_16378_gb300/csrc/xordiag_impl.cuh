@@ -258,6 +258,15 @@ struct ArC128 {
   __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
     reinterpret_cast<double2*>(p)[i] = out_value(a, cv, k);
   }
+  __device__ static __forceinline__ void store_value(void* p, unsigned long long i, const double2& o) {
+    reinterpret_cast<double2*>(p)[i] = o;
+  }
+  // Loaded element times a real factor f (one FP64 rounding per part).
+  __device__ static __forceinline__ Raw weigh(const Raw& r, double f) {
+    const double re = __hiloint2double((int)r.y, (int)r.x) * f, im = __hiloint2double((int)r.w, (int)r.z) * f;
+    return make_uint4((uint32_t)__double2loint(re), (uint32_t)__double2hiint(re), (uint32_t)__double2loint(im),
+                      (uint32_t)__double2hiint(im));
+  }
   // Same, with an L2 cache policy (createpolicy) for the store.
   __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
                                                     uint32_t k, uint64_t pol) {
@@ -331,6 +340,10 @@ struct ArC64 {
   __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
     reinterpret_cast<float2*>(p)[i] = out_value(a, cv, k);
   }
+  __device__ static __forceinline__ void store_value(void* p, unsigned long long i, const float2& o) {
+    reinterpret_cast<float2*>(p)[i] = o;
+  }
+  __device__ static __forceinline__ Raw weigh(const Raw& r, float f) { return make_float2(r.x * f, r.y * f); }
   __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
                                                     uint32_t k, uint64_t pol) {
     const float2 o = out_value(a, cv, k);
@@ -454,14 +467,67 @@ struct Addr {
 };
 
 
+// ------------------------------------------------- fused work at the two ends of a unit --
+// Arguments of the fused forms (kernel parameters; unused by NoEpi).
+struct EpiArgs {
+  const void* w;     // 4^N real weights: double (complex128) or float (complex64)
+  const void* g;     // one real scaling the weights (compose), or nullptr for 1
+  double* partial;   // one partial loss per work unit (decompose)
+};
+// Plain decomposition / composition.
+struct NoEpi {
+  static constexpr bool kWeightIn = false, kNormOut = false;
+};
+// Composition of weighted coefficients: each loaded c_n is multiplied by g w_n first.
+struct WeightInEpi {
+  static constexpr bool kWeightIn = true, kNormOut = false;
+};
+// Decomposition that also accumulates sum_n w_n |c_n|^2 over the coefficients it stores.
+struct NormOutEpi {
+  static constexpr bool kWeightIn = false, kNormOut = true;
+};
+
+// Per-thread accumulator of w_n |c_n|^2: FP64 for complex128; for complex64 a TwoSum-compensated
+// FP32 pair, read out in FP64.
+template <class AR>
+struct NormAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(const double2& o, double w) { s = fma(w, fma(o.y, o.y, o.x * o.x), s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct NormAcc<ArC64> {
+  float s = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(const float2& o, float w) {
+    const float x = w * fmaf(o.y, o.y, o.x * o.x);
+    const float t = s + x, bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
+template <class AR>
+struct RealOf {
+  using T = double;
+};
+template <>
+struct RealOf<ArC64> {
+  using T = float;
+};
+
 // ------------------------------------------------------------- one single-CTA work unit --
 // Classes [xb, xb + 2^K) of the N-qubit matrix whose elements start at index `base` of in/out
 // (decompose: in = G, out = c; compose: in = c, out = G). smax holds 2^K words. prefetch()
 // is called once the unit's own loads are in flight.
-template <int UB, int RB, int N, class AR, bool COMPOSE, class Prefetch>
-__device__ __forceinline__ void run_unit(const void* __restrict__ in, void* __restrict__ out, unsigned long long base,
-                                         uint32_t xb, int scale_exp, uint32_t xaddr, uint32_t* smax, uint32_t t,
-                                         Prefetch prefetch) {
+// EPI adds the fused work of WeightInEpi (compose) or NormOutEpi (decompose; the return value is
+// then this thread's share of the unit's partial loss, else 0).
+template <int UB, int RB, int N, class AR, bool COMPOSE, class Prefetch, class EPI = NoEpi>
+__device__ __forceinline__ double run_unit(const void* __restrict__ in, void* __restrict__ out,
+                                           unsigned long long base, uint32_t xb, int scale_exp, uint32_t xaddr,
+                                           uint32_t* smax, uint32_t t, Prefetch prefetch,
+                                           const EpiArgs& ea = EpiArgs{nullptr, nullptr, nullptr}) {
+  using Real = typename RealOf<AR>::T;
+  constexpr unsigned long long kNMask = (1ull << (2 * N)) - 1ull;
   using LY = Layout<UB, N, RB>;
   constexpr int K = LY::K;
   constexpr int E = LY::E;
@@ -477,10 +543,18 @@ __device__ __forceinline__ void run_unit(const void* __restrict__ in, void* __re
   typename AR::Raw raw[E];
   uint32_t emax = 0;
 #pragma unroll
-  for (int j = 0; j < E; ++j) {
-    raw[j] = AR::load(in, ain.at(LY::reg_u(0, j) >> K));
-    emax = max(emax, AR::exp_key(raw[j]));
+  for (int j = 0; j < E; ++j) raw[j] = AR::load(in, ain.at(LY::reg_u(0, j) >> K));
+  if constexpr (EPI::kWeightIn) {
+    const Real* w = static_cast<const Real*>(ea.w);
+    const Real g = ea.g ? *static_cast<const Real*>(ea.g) : Real(1);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const Real wn = w[ain.at(LY::reg_u(0, j) >> K) & kNMask];
+      raw[j] = AR::weigh(raw[j], g == Real(1) ? wn : g * wn);
+    }
   }
+#pragma unroll
+  for (int j = 0; j < E; ++j) emax = max(emax, AR::exp_key(raw[j]));
   prefetch();
   uint32_t Ekey = 0;
   if constexpr (AR::kScaled) {
@@ -509,9 +583,23 @@ __device__ __forceinline__ void run_unit(const void* __restrict__ in, void* __re
   BitSum<LY::regrow(LAST, 0), LY::regrow(LAST, 1), LY::regrow(LAST, 2), LY::regrow(LAST, 3)> xo;
   xo.init(x);
   const uint32_t ko = COMPOSE ? 0u : (uint32_t)__popc(x & yl);
+  if constexpr (EPI::kNormOut) {
+    const Real* w = static_cast<const Real*>(ea.w);
+    NormAcc<AR> acc;
 #pragma unroll
-  for (int j = 0; j < E; ++j)
-    AR::store(out, ao.at(LY::reg_u(LAST, j) >> K), v[j], cv, COMPOSE ? 0u : ko + xo.at(j));
+    for (int j = 0; j < E; ++j) {
+      const unsigned long long i = ao.at(LY::reg_u(LAST, j) >> K);
+      const auto o = AR::out_value(v[j], cv, ko + xo.at(j));
+      AR::store_value(out, i, o);
+      acc.add(o, w[i & kNMask]);
+    }
+    return acc.value();
+  } else {
+#pragma unroll
+    for (int j = 0; j < E; ++j)
+      AR::store(out, ao.at(LY::reg_u(LAST, j) >> K), v[j], cv, COMPOSE ? 0u : ko + xo.at(j));
+    return 0.0;
+  }
 }
 
 // L2 prefetch of the elements run_unit will load for classes [xb, xb + 2^K).

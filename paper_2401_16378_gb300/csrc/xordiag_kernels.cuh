@@ -13,10 +13,12 @@ using namespace xd;
 // order: neighbouring units share DRAM lines (a 128-byte line holds 8 consecutive classes of
 // a row), and CTAs launched together read them close in time. Each CTA prefetches into L2
 // the unit one resident wave ahead -- the unit that will run on an SM after this wave.
-template <int UB, int RB, int N, class AR, bool COMPOSE>
+// EPI: NoEpi, or the fused forms (WeightInEpi for compose; NormOutEpi for decompose, which
+// writes the unit's partial loss to ea.partial[unit] in a fixed order).
+template <int UB, int RB, int N, class AR, bool COMPOSE, class EPI = NoEpi>
 __global__ void __launch_bounds__(Unit<UB, RB>::kThreads, Unit<UB, RB>::kMinBlocks)
     xordiag_kernel(const void* __restrict__ in, void* __restrict__ out, int scale_exp, unsigned long long units,
-                   unsigned long long ahead) {
+                   unsigned long long ahead, EpiArgs ea) {
   using LY = Layout<UB, N, RB>;
   constexpr int K = LY::K;
   constexpr uint32_t D = 1u << N;
@@ -32,8 +34,26 @@ __global__ void __launch_bounds__(Unit<UB, RB>::kThreads, Unit<UB, RB>::kMinBloc
       unit_prefetch<UB, RB, N, AR, COMPOSE>(in, (nu / units_per_mat) * (unsigned long long)D * D,
                                             (uint32_t)(nu % units_per_mat) << K, t);
   };
-  run_unit<UB, RB, N, AR, COMPOSE>(in, out, (unit / units_per_mat) * (unsigned long long)D * D,
-                                   (uint32_t)(unit % units_per_mat) << K, scale_exp, xaddr, smax, t, prefetch_ahead);
+  const unsigned long long base = (unit / units_per_mat) * (unsigned long long)D * D;
+  const double part = run_unit<UB, RB, N, AR, COMPOSE, decltype(prefetch_ahead), EPI>(
+      in, out, base, (uint32_t)(unit % units_per_mat) << K, scale_exp, xaddr, smax, t, prefetch_ahead, ea);
+  if constexpr (EPI::kNormOut) {
+    // fixed-tree block sum of the threads' shares
+    __shared__ double wsum[Unit<UB, RB>::kThreads / 32];
+    double v = part;
+#pragma unroll
+    for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+    if ((t & 31u) == 0) wsum[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) {
+      double tot = 0.0;
+#pragma unroll
+      for (int i = 0; i < Unit<UB, RB>::kThreads / 32; ++i) tot += wsum[i];
+      ea.partial[unit] = tot;
+    }
+  } else {
+    (void)part;
+  }
 }
 
 // ------------------------------------------------------------------------- CTA clusters --
@@ -190,10 +210,11 @@ static int device_sms() {
   return sms;
 }
 
-template <int UB, int RB, int N, class AR, bool COMPOSE>
-cudaError_t launch_one(const void* in, long long count, int scale_exp, void* out, cudaStream_t st) {
+template <int UB, int RB, int N, class AR, bool COMPOSE, class EPI = NoEpi>
+cudaError_t launch_one(const void* in, long long count, int scale_exp, void* out, cudaStream_t st,
+                       EpiArgs ea = EpiArgs{nullptr, nullptr, nullptr}) {
   constexpr size_t smem = Unit<UB, RB>::kSmem;
-  auto kern = xordiag_kernel<UB, RB, N, AR, COMPOSE>;
+  auto kern = xordiag_kernel<UB, RB, N, AR, COMPOSE, EPI>;
   static int resident = 0;  // CTAs per SM (one device per process in this library)
   if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -206,7 +227,7 @@ cudaError_t launch_one(const void* in, long long count, int scale_exp, void* out
   const unsigned long long units = (unsigned long long)count * ((1ull << (2 * N)) >> UB);
   if (units > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
   const unsigned long long ahead = (unsigned long long)device_sms() * resident;
-  kern<<<(unsigned)units, Unit<UB, RB>::kThreads, smem, st>>>(in, out, scale_exp, units, ahead);
+  kern<<<(unsigned)units, Unit<UB, RB>::kThreads, smem, st>>>(in, out, scale_exp, units, ahead, ea);
   return cudaGetLastError();
 }
 

@@ -69,7 +69,11 @@ def test_decompose_rejects_bad_arguments(lib):
     assert lib.pauli_decompose(P(A), 4, 1, C128, P(B), 9, None) == ARG
     assert lib.pauli_decompose(P(A), 3, 1, C128, P(B), 2, None) == UNSUP  # no XOR-diagonal kernel at N=3
     assert lib.pauli_set_variant(5, C128, 0, 1) == UNSUP
-    assert lib.pauli_set_variant(14, C128, 2, 1) == ARG
+    assert lib.pauli_set_variant(14, C128, 4, 1) == ARG
+    assert lib.pauli_get_variant(10, C128, 0) == 1  # one matrix: 8192-element units
+    assert lib.pauli_get_variant(10, C128, 2) == 2  # a batch: 4096-element units, two CTAs per SM
+    assert lib.pauli_get_variant(14, C128, 2) == 6
+    assert lib.pauli_set_variant(14, C128, 3, 5) == UNSUP
     assert lib.pauli_get_variant(3, C128, 0) == 0
     assert lib.pauli_get_variant(14, C128, 0) == 6  # decompose at N = 14: the tiled kernel
     assert lib.pauli_get_variant(14, C128, 1) == 1  # compose: single-pass 8192-element units
@@ -103,6 +107,17 @@ def test_hermitian_and_norm_reject_bad_arguments(lib):
     assert lib.pauli_weighted_norm_grad(P(A), 4, 1, C128, P(B), None, P(A + 16), None) == ALIAS
     assert lib.pauli_weighted_norm_grad(P(A), 4, 1, C128, P(B), None, P(B + 16), None) == ALIAS  # over w
     assert lib.pauli_weighted_norm_grad(P(A), 4, 1, C128, P(B), P(B + 4), P(B + 65536), None) == ALIGN
+    # fused forms: c at B, w at B + 1 MiB, loss at B + 2 MiB
+    W, L = B + (1 << 20), B + (2 << 20)
+    assert lib.pauli_decompose_weighted_norm(P(A), 4, 1, C128, P(B), None, P(L), 0, None) == NULL
+    assert lib.pauli_decompose_weighted_norm(P(A), 4, 1, C128, P(B), P(W), None, 0, None) == NULL
+    assert lib.pauli_decompose_weighted_norm(P(A), 4, 1, C128, P(B), P(W), P(B + 64), 0, None) == ALIAS
+    assert lib.pauli_decompose_weighted_norm(P(A), 4, 1, C128, P(B), P(B + 16), P(L), 0, None) == ALIAS
+    assert lib.pauli_decompose_weighted_norm(P(A), 4, 1, C128, P(B), P(W + 4), P(L), 0, None) == ALIGN
+    assert lib.pauli_compose_weighted(P(1 << 32), 13, 1, C128, P(3 << 32), None, P(2 << 32), 0, None) == UNSUP
+    assert lib.pauli_compose_weighted(P(A), 4, 1, C128, None, None, P(B), 0, None) == NULL
+    assert lib.pauli_compose_weighted(P(A), 4, 1, C128, P(W), None, P(B), 65, None) == ARG
+    assert lib.pauli_compose_weighted(P(A), 4, 1, C128, P(B + 32), None, P(B), 0, None) == ALIAS
 
 
 def test_coeffs_at_rejects_bad_arguments(lib):

@@ -111,7 +111,8 @@ def test_adjoint_chain_matches_oracle(N, count, dtype):
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
 
 
-def test_adjoint_workload_full_size():
+@pytest.mark.parametrize("fused", [True, False])
+def test_adjoint_workload_full_size(fused):
     """64 matrices at N = 10 (the adjoint workload, same calls as the benchmark): the loss
     against the oracle's per-matrix norms of the GPU coefficients, the coefficients and the
     gradient at sampled entries against the oracle."""
@@ -119,8 +120,11 @@ def test_adjoint_workload_full_size():
     A = workloads.adjoint_inputs(workloads.SEEDS["adjoint"], batch=B, N=N)
     w = workloads.adjoint_weights(workloads.SEEDS["adjoint_w"], N)
     Gt = _dev(A).requires_grad_(True)
-    c = pg.decompose_autograd(Gt)
-    loss = pg.weighted_norm_autograd(c, _dev(w))
+    if fused:
+        loss, c = pg.decompose_weighted_norm_autograd(Gt, _dev(w))
+    else:
+        c = pg.decompose_autograd(Gt)
+        loss = pg.weighted_norm_autograd(c, _dev(w))
     loss.backward()
     ch = c.detach().cpu().numpy()
     want_loss = sum(oracle.weighted_norm(ch[k], w) for k in range(B))
@@ -136,3 +140,107 @@ def test_adjoint_workload_full_size():
     for k in (0, 63):
         want = oracle.compose_at(oracle.weighted_norm_grad(ch[k], w), rows, cols) * 2.0 ** -N
         assert np.max(np.abs(gh[k][rows, cols] - want)) <= 1e-12 * np.max(np.abs(want)) * 4
+
+
+# ----------------------------------------------------------------------------- fused forms --
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("N,count", [(3, 2), (6, 1), (7, 5), (10, 3), (11, 2), (12, 1), (12, 2)])
+def test_decompose_weighted_norm_matches_oracle(N, count, dtype):
+    """One fused pass (N 6..12) or decomposition + norm (N < 6): the coefficients equal the plain
+    decomposition's (bit for bit in complex128: every single-pass shape computes identical
+    values) and the loss the oracle's norm of them."""
+    G = np.stack([workloads.gaussian_complex(N, 960 + k) for k in range(count)]).astype(NP[dtype])
+    w = workloads.adjoint_weights(961 + N, N).astype(RT[dtype])
+    Gd = _dev(G)
+    c, loss = pg.decompose_weighted_norm(Gd, _dev(w))
+    ch = c.cpu().numpy()
+    ref = pg.decompose(Gd).cpu().numpy()
+    if dtype == torch.complex128:
+        np.testing.assert_array_equal(ch, ref)
+    else:
+        assert np.max(np.abs(ch - ref)) <= 2e-6 * np.max(np.abs(G))
+    want = oracle.weighted_norm(ch, w)
+    assert abs(float(loss.cpu()) - want) <= LOSS_TOL[dtype] * want
+    idx = workloads.sample_indices(N, 962, k=128)
+    want_c = oracle.decompose_at(G[0].astype(np.complex128), idx)
+    tol = {torch.complex128: 1e-12, torch.complex64: 2e-6}[dtype]
+    assert np.max(np.abs(ch[0][idx.astype(np.int64)] - want_c)) <= tol * np.max(np.abs(G[0]))
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("N,count", [(2, 3), (5, 2), (6, 1), (8, 4), (10, 3), (12, 1)])
+def test_compose_weighted_matches_grad_then_compose(N, count, dtype):
+    """compose_weighted(c, w, g, 1 - N) = compose(weighted_norm_grad(c, w, g), -N): bit for bit
+    in complex128; and at sampled entries against the oracle's 2^-N compose(2 g w c)."""
+    c = _coeffs(N, count, 970 + N, dtype)
+    w = workloads.adjoint_weights(971 + N, N).astype(RT[dtype])
+    g = np.array([0.625], dtype=RT[dtype])
+    cd, wd, gd = _dev(c), _dev(w), _dev(g)
+    got = pg.compose_weighted(cd, wd, gd, scale_exp=1 - N).cpu().numpy()
+    two = pg.compose(pg.weighted_norm_grad(cd, wd, gd), scale_exp=-N).cpu().numpy()
+    scale = np.max(np.abs(two))
+    if dtype == torch.complex128:
+        np.testing.assert_array_equal(got, two)
+    else:
+        assert np.max(np.abs(got - two)) <= 1e-5 * scale
+    D = 1 << N
+    rows = np.arange(0, D, max(1, D // 64))
+    cols = (rows * 5 + 1) % D
+    for k in (0, count - 1):
+        want = oracle.compose_at(oracle.weighted_norm_grad(c[k], w.astype(np.float64), 0.625), rows, cols) * 2.0 ** -N
+        tol = {torch.complex128: 1e-12, torch.complex64: 1e-5}[dtype]
+        assert np.max(np.abs(got[k][rows, cols] - want)) <= tol * np.max(np.abs(want)) * max(1, N)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("N,count", [(4, 3), (6, 2), (10, 2)])
+def test_fused_adjoint_chain_matches_oracle(N, count, dtype):
+    """decompose_weighted_norm_autograd: L and dL/dG against the oracle (fused kernels for
+    N >= 6; the plain weighted composition below)."""
+    G = np.stack([workloads.gaussian_complex(N, 980 + k) for k in range(count)]).astype(NP[dtype])
+    w = workloads.adjoint_weights(981, N)
+    Gt = _dev(G).requires_grad_(True)
+    loss, c = pg.decompose_weighted_norm_autograd(Gt, _dev(w.astype(RT[dtype])))
+    assert not c.requires_grad
+    (3.0 * loss).backward()
+    w_used = w.astype(RT[dtype]).astype(np.float64)
+    tol = {torch.complex128: 1e-12, torch.complex64: 1e-5}[dtype]
+    if N <= 6:
+        c_ref = np.stack([oracle.decompose_full(G[k].astype(np.complex128)) for k in range(count)])
+        want_loss = oracle.weighted_norm(c_ref, w_used)
+        want = np.stack([oracle.decompose_grad(oracle.weighted_norm_grad(c_ref[k], w_used, 3.0)) for k in range(count)])
+        got = Gt.grad.cpu().numpy()
+        assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+    else:
+        ch = c.cpu().numpy()
+        want_loss = oracle.weighted_norm(ch, w_used)
+        D = 1 << N
+        rows = np.arange(0, D, 29)
+        cols = (rows * 3 + 7) % D
+        got = Gt.grad.cpu().numpy()
+        for k in range(count):
+            want = oracle.compose_at(oracle.weighted_norm_grad(ch[k], w_used, 3.0), rows, cols) * 2.0 ** -N
+            assert np.max(np.abs(got[k][rows, cols] - want)) <= tol * np.max(np.abs(want)) * N
+    assert abs(float(loss.detach().cpu()) - want_loss) <= tol * want_loss
+
+
+def test_fused_adjoint_falls_back_above_n12():
+    """N = 13: the forward is the tiled decomposition + the norm, the backward the gradient +
+    composition (no fused kernel at this size); checked at sampled entries."""
+    N = 13
+    G = workloads.gaussian_complex(N, 990)
+    w = workloads.adjoint_weights(991, N)
+    Gt = _dev(G).requires_grad_(True)
+    loss, c = pg.decompose_weighted_norm_autograd(Gt, _dev(w))
+    loss.backward()
+    ch = c.cpu().numpy()
+    want_loss = oracle.weighted_norm(ch, w)
+    assert abs(float(loss.detach().cpu()) - want_loss) <= 1e-12 * want_loss
+    idx = workloads.sample_indices(N, 992, k=64)
+    assert np.max(np.abs(ch[idx.astype(np.int64)] - oracle.decompose_at(G, idx))) <= 1e-12 * np.max(np.abs(G))
+    # dL/dG = 2^-N compose(2 w c), so its coefficients are 2^(1-N) w c: decompose sampled
+    # coefficients of the GPU gradient with the oracle (O(2^N) each at this size)
+    gidx = workloads.sample_indices(N, 993, k=64)
+    want = 2.0 ** (1 - N) * w[gidx.astype(np.int64)] * ch[gidx.astype(np.int64)]
+    got = oracle.decompose_at(Gt.grad.cpu().numpy(), gidx)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))

@@ -115,12 +115,12 @@ def test_tiled_batch_and_repeated_launches(dtype):
     N = 12
     Gs = np.stack([workloads.gaussian_complex(N, 2600 + b) for b in range(3)]).astype(NP[dtype])
     Gd = dev(Gs)
-    pg.set_variant(N, dtype, "decompose", "tiled8")
+    pg.set_variant(N, dtype, "decompose_batched", "tiled8")
     try:
         outs = [host(pg.decompose(Gd, method="xordiag")) for _ in range(3)]
         pg.stream_status()
     finally:
-        pg.set_variant(N, dtype, "decompose", "default")
+        pg.set_variant(N, dtype, "decompose_batched", "default")
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
     idx = workloads.sample_indices(N, 2601, k=256)
