@@ -359,12 +359,15 @@ class PauliDecomposeWeightedNorm(torch.autograd.Function):
         c, loss = pauli_decompose_weighted_norm(G.contiguous(), w, method=method)
         ctx.save_for_backward(c, w)
         ctx.mark_non_differentiable(c)
+        ctx.set_materialize_grads(False)  # no zero-filled gradient for c (a full pass over c)
         return loss, c
 
     @staticmethod
     def backward(ctx, g: torch.Tensor, _grad_c):
         c, w = ctx.saved_tensors
         N = _qubits_of_coeffs(c)
+        if g is None:
+            return None, None, None
         g = g.contiguous()
         if N <= 12:
             return pauli_compose_weighted(c, w, g, scale_exp=1 - N), None, None
