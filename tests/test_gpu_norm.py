@@ -244,3 +244,29 @@ def test_fused_adjoint_falls_back_above_n12():
     want = 2.0 ** (1 - N) * w[gidx.astype(np.int64)] * ch[gidx.astype(np.int64)]
     got = oracle.decompose_at(Gt.grad.cpu().numpy(), gidx)
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_fused_nonfinite_and_zero_weights():
+    """A NaN in G makes its class's coefficients and the loss NaN (as in the separate calls);
+    zero weights drop their coefficients from the loss and from the weighted composition."""
+    N = 8
+    G = workloads.gaussian_complex(N, 995)
+    w = workloads.adjoint_weights(996, N)
+    Gn = G.copy()
+    Gn[3, 17] = np.nan
+    c, loss = pg.decompose_weighted_norm(_dev(Gn), _dev(w))
+    assert np.isnan(float(loss.cpu()))
+    ch = c.cpu().numpy()
+    ref = pg.decompose(_dev(Gn)).cpu().numpy()
+    np.testing.assert_array_equal(np.isnan(ch), np.isnan(ref))
+    wz = w.copy()
+    wz[::3] = 0.0
+    c, loss = pg.decompose_weighted_norm(_dev(G), _dev(wz))
+    ch = c.cpu().numpy()
+    want = oracle.weighted_norm(ch, wz)
+    assert abs(float(loss.cpu()) - want) <= 1e-12 * want
+    cz = ch.copy()
+    cz[::3] = 0.0
+    a = pg.compose_weighted(_dev(ch), _dev(wz)).cpu().numpy()
+    b = pg.compose_weighted(_dev(cz), _dev(wz)).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
