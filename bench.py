@@ -454,6 +454,13 @@ def n12_forms(pg, workloads, dev, oracle, timed, forms):
                 "ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3), "max_err_rel": err,
                 "hbm_gbs_algorithmic": 4 ** N * (16 + 8) / (ms * 1e-3) / 1e9,
                 "max_abs_imag_dropped_rel": float(np.max(np.abs(want.imag)) / np.max(np.abs(G)))}
+            # upper triangle only (pauli_decompose_hermitian_upper): 8 B read + 8 B written
+            ms = timed(lambda: pg.decompose_hermitian(g, out=r, upper=True), 20)
+            err = float(np.max(np.abs(r.cpu().numpy()[idx.astype(np.int64)] - want.real)) / np.max(np.abs(G)))
+            forms["n12_hermitian_xordiag_upper_c128"] = {
+                "ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3), "max_err_rel": err,
+                "hbm_gbs_algorithmic": 4 ** N * (8 + 8) / (ms * 1e-3) / 1e9,
+                "reads": "diagonal and upper triangle of G only"}
             del r
         del g, o
 

@@ -88,6 +88,21 @@ int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int m
  * size (8192 or 4096 elements; always 4096 at N = 6) and 16 elements per thread. */
 int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* out_re, int method, void* stream);
 
+/* The same for matrices known to be Hermitian, read from the upper triangle only: the real
+ * parts of the diagonal and the elements above it (q > r). The strict lower triangle is never
+ * read and the diagonal's imaginary parts are never used: both may hold anything.
+ *   out_re[k * 4^N + n] = c_n of the Hermitian matrix with that upper triangle   Eq. (4), (13).
+ * For an XY-mask x != 0 with top set bit h the XOR-diagonal satisfies e_x[r ^ x] = conj(e_x[r]);
+ * the rows with bit h clear are exactly the upper-triangle elements of the class, and one
+ * Walsh-Hadamard transform over the other N - 1 row bits gives two real coefficients per
+ * value: c(x, z) = 2^(1-N) Re(V[z without bit h] i^popc(x & z)) for z_h = 0 and 1. So the
+ * XOR-diagonal kernel reads half of G and writes reals: 16 bytes per complex128 coefficient
+ * instead of 32. N <= 12 (PAULI_ERR_UNSUPPORTED above); the XOR-diagonal kernel covers N 7..12,
+ * smaller N and PAULI_PLAIN take the per-coefficient sum with the lower triangle read through
+ * its mirror. Arguments as for pauli_decompose_hermitian. */
+int pauli_decompose_hermitian_upper(const void* G, int N, int count, int dtype, void* out_re, int method,
+                                    void* stream);
+
 /* Compose: G_out[k] = 2^scale_exp * sum_n c[k * 4^N + n] P_n                         Eq. (1).
  * scale_exp in [-64, 64] is an exact power-of-two factor; scale_exp = -N gives the adjoint
  * of pauli_decompose (the gradient of a real loss with respect to G is

@@ -75,10 +75,11 @@ def pauli_decompose(G: torch.Tensor, out: torch.Tensor | None = None, method="au
     return out
 
 
-def pauli_decompose_hermitian(G: torch.Tensor, out: torch.Tensor | None = None, method="auto",
-                              stream=None) -> torch.Tensor:
+def pauli_decompose_hermitian(G: torch.Tensor, out: torch.Tensor | None = None, method="auto", stream=None,
+                              upper: bool = False) -> torch.Tensor:
     """Re c_n for a (..., 2^N, 2^N) complex CUDA tensor (all of c_n when G is Hermitian); returns
-    a real (..., 4^N) tensor of G's precision."""
+    a real (..., 4^N) tensor of G's precision. upper=True: G is Hermitian and only its upper
+    triangle (and the diagonal's real parts) is read -- half the bytes (N <= 12)."""
     _device_tensor(G, "G")
     N = _qubits_of_matrix(G)
     count = G.numel() // (4 ** N)
@@ -90,8 +91,8 @@ def pauli_decompose_hermitian(G: torch.Tensor, out: torch.Tensor | None = None, 
     _device_tensor(out, "out")
     if out.dtype != rdt or out.numel() != G.numel():
         raise ValueError("out must hold one real of G's precision per coefficient")
-    check(_lib.load().pauli_decompose_hermitian(G.data_ptr(), N, count, _dtype(G), out.data_ptr(), _method(method),
-                                                _stream(stream)))
+    fn = _lib.load().pauli_decompose_hermitian_upper if upper else _lib.load().pauli_decompose_hermitian
+    check(fn(G.data_ptr(), N, count, _dtype(G), out.data_ptr(), _method(method), _stream(stream)))
     return out
 
 

@@ -160,6 +160,35 @@ int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* 
   return PAULI_OK;
 }
 
+int pauli_decompose_hermitian_upper(const void* G, int N, int count, int dtype, void* out_re, int method,
+                                    void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (count < 1) return fail(PAULI_ERR_ARG, "count = %d must be >= 1", count);
+  if (!G) return fail(PAULI_ERR_NULL, "G is NULL");
+  if (!out_re) return fail(PAULI_ERR_NULL, "out_re is NULL");
+  const size_t es = elem_bytes(dtype);
+  if ((st = check_aligned(G, es, "G"))) return st;
+  if ((st = check_aligned(out_re, es / 2, "out_re"))) return st;
+  const unsigned long long per = 1ull << (2 * N);
+  if ((unsigned long long)count > (~0ull / es) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
+  const size_t in_bytes = (size_t)(per * (unsigned long long)count) * es;
+  if (overlaps(G, in_bytes, out_re, in_bytes / 2)) return fail(PAULI_ERR_ALIAS, "G and out_re overlap");
+  if (method != PAULI_AUTO && method != PAULI_PLAIN && method != PAULI_XORDIAG)
+    return fail(PAULI_ERR_ARG, "method %d is not a pauli_method", method);
+  if (N > 12) return fail(PAULI_ERR_UNSUPPORTED, "pauli_decompose_hermitian_upper is built for N <= 12, not N = %d", N);
+  if (method == PAULI_XORDIAG && N < 7)
+    return fail(PAULI_ERR_UNSUPPORTED, "the upper-triangle XOR-diagonal kernel starts at N = 7");
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  const bool c64 = dtype == PAULI_C64;
+  cudaError_t e = (method == PAULI_PLAIN || N < 7)
+                      ? pauli::launch_plain_decompose(G, N, count, c64, out_re, (cudaStream_t)stream, true, true)
+                      : pauli::launch_xordiag_herm_upper(G, N, count, c64, out_re, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_hermitian_upper launch");
+  return PAULI_OK;
+}
+
 int pauli_compose(const void* c, int N, int count, int dtype, void* G_out, int scale_exp, void* stream) {
   int st = check_pair(c, "c", N, count, dtype, G_out, "G_out");
   if (st) return st;

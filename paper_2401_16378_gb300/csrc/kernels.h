@@ -6,9 +6,12 @@
 namespace pauli {
 
 // Eq. (13) per coefficient, Gray-code order (plain.cu).
-// re: store only Re c_n, into count * 4^N reals.
+// re: store only Re c_n, into count * 4^N reals; upper (with re): G Hermitian, read from its
+// upper triangle.
 cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s,
-                                   bool re = false);
+                                   bool re = false, bool upper = false);
+// Hermitian G read from its upper triangle, real coefficients, N = 7..12 (xordiag_herm_*.cu).
+cudaError_t launch_xordiag_herm_upper(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s);
 // w, g (nullable): compose g w_n c_n instead of c_n.
 cudaError_t launch_plain_compose(const void* c, int N, long long count, bool c64, int scale_exp, void* G,
                                 cudaStream_t s, const void* w = nullptr, const void* g = nullptr);

@@ -66,8 +66,10 @@ struct AccC64 {
   __device__ __forceinline__ double total_im(int k) const { return (double)si[k] + (double)ei[k]; }
 };
 
-// RE: store only Re c_n, into an array of reals (Hermitian decomposition).
-template <bool C64, bool RE>
+// RE: store only Re c_n, into an array of reals (Hermitian decomposition). UPPER (with RE): G is
+// Hermitian and read from its upper triangle; an element below the diagonal, G[r, r ^ x] with
+// bit h of r set (h the top set bit of x), is read as conj(G[r ^ x, r]).
+template <bool C64, bool RE, bool UPPER = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(const void* __restrict__ Gv, int N,
                                                                              long long count, void* __restrict__ outv) {
   using Acc = typename std::conditional<C64, AccC64, AccC128>::type;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
   const uint32_t x = (uint32_t)(tile / tiles_z) * CW + c;
   const uint32_t zb = (uint32_t)(tile % tiles_z) * KZ;
 
+  const uint32_t hx = x ? 31u - (uint32_t)__clz(x) : 32u;  // top set bit of x (UPPER)
   Acc acc;
   acc.zero();
   if (active) {
@@ -110,7 +113,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
           signs ^= flip & kmask;
         }
         const uint32_t r = rsub | ((g ^ (g >> 1)) << lrs);
-        const float2 e = __ldg(&G[(unsigned long long)r * D + (r ^ x)]);
+        float2 e;
+        if (UPPER && hx < 32u && ((r >> hx) & 1u)) {
+          e = __ldg(&G[(unsigned long long)(r ^ x) * D + r]);
+          e.y = -e.y;
+        } else {
+          e = __ldg(&G[(unsigned long long)r * D + (r ^ x)]);
+          if (UPPER && x == 0u) e.y = 0;  // the diagonal: its imaginary parts are not used
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           if ((uint32_t)k < KZ) acc.add(k, e.x, e.y, (signs >> k) & 1u);
@@ -124,7 +134,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
           signs ^= flip & kmask;
         }
         const uint32_t r = rsub | ((g ^ (g >> 1)) << lrs);
-        const double2 e = __ldg(&G[(unsigned long long)r * D + (r ^ x)]);
+        double2 e;
+        if (UPPER && hx < 32u && ((r >> hx) & 1u)) {
+          e = __ldg(&G[(unsigned long long)(r ^ x) * D + r]);
+          e.y = -e.y;
+        } else {
+          e = __ldg(&G[(unsigned long long)r * D + (r ^ x)]);
+          if (UPPER && x == 0u) e.y = 0;  // the diagonal: its imaginary parts are not used
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           if ((uint32_t)k < KZ) acc.add(k, e.x, e.y, (signs >> k) & 1u);
@@ -291,13 +308,15 @@ __global__ void __launch_bounds__(256) plain_compose_kernel(const void* __restri
 }  // namespace
 
 cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s,
-                                   bool re) {
+                                   bool re, bool upper) {
   const int lcw = N < 3 ? N : 3, lkz = lcw;
   const unsigned long long tiles = ((1ull << N) >> lcw) * ((1ull << N) >> lkz) * (unsigned long long)count;
   const unsigned long long blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-  auto kern = c64 ? (re ? plain_decompose_kernel<true, true> : plain_decompose_kernel<true, false>)
-                  : (re ? plain_decompose_kernel<false, true> : plain_decompose_kernel<false, false>);
+  auto kern = c64 ? (re ? (upper ? plain_decompose_kernel<true, true, true> : plain_decompose_kernel<true, true>)
+                        : plain_decompose_kernel<true, false>)
+                  : (re ? (upper ? plain_decompose_kernel<false, true, true> : plain_decompose_kernel<false, true>)
+                        : plain_decompose_kernel<false, false>);
   kern<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
   return cudaGetLastError();
 }

@@ -41,6 +41,8 @@ cudaError_t xordiag_c64_decompose(int, int, const void*, long long, int, void*, 
 cudaError_t xordiag_c64_compose(int, int, const void*, long long, int, void*, cudaStream_t);
 cudaError_t xordiag_re_decompose_c128(int, const void*, long long, void*, cudaStream_t, bool);
 cudaError_t xordiag_re_decompose_c64(int, const void*, long long, void*, cudaStream_t, bool);
+cudaError_t xordiag_herm_upper_c128(int, const void*, long long, void*, cudaStream_t);
+cudaError_t xordiag_herm_upper_c64(int, const void*, long long, void*, cudaStream_t);
 
 namespace {
 
@@ -122,6 +124,10 @@ cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, 
   const bool unit4096 = (v == kVariantUnit12 || v == kVariantUnit12x8) && N <= 14;
   return c64 ? xordiag_re_decompose_c64(N, in, count, out, s, unit4096)
              : xordiag_re_decompose_c128(N, in, count, out, s, unit4096);
+}
+
+cudaError_t launch_xordiag_herm_upper(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s) {
+  return c64 ? xordiag_herm_upper_c64(N, G, count, out, s) : xordiag_herm_upper_c128(N, G, count, out, s);
 }
 
 }  // namespace pauli

@@ -261,6 +261,8 @@ struct ArC128 {
   __device__ static __forceinline__ void store_value(void* p, unsigned long long i, const double2& o) {
     reinterpret_cast<double2*>(p)[i] = o;
   }
+  __device__ static __forceinline__ Raw conj(const Raw& r) { return make_uint4(r.x, r.y, r.z, r.w ^ 0x80000000u); }
+  __device__ static __forceinline__ Raw real_part(const Raw& r) { return make_uint4(r.x, r.y, 0u, 0u); }
   // Loaded element times a real factor f (one FP64 rounding per part).
   __device__ static __forceinline__ Raw weigh(const Raw& r, double f) {
     const double re = __hiloint2double((int)r.y, (int)r.x) * f, im = __hiloint2double((int)r.w, (int)r.z) * f;
@@ -344,6 +346,8 @@ struct ArC64 {
     reinterpret_cast<float2*>(p)[i] = o;
   }
   __device__ static __forceinline__ Raw weigh(const Raw& r, float f) { return make_float2(r.x * f, r.y * f); }
+  __device__ static __forceinline__ Raw conj(const Raw& r) { return make_float2(r.x, -r.y); }
+  __device__ static __forceinline__ Raw real_part(const Raw& r) { return make_float2(r.x, 0.f); }
   __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
                                                     uint32_t k, uint64_t pol) {
     const float2 o = out_value(a, cv, k);
@@ -476,15 +480,20 @@ struct EpiArgs {
 };
 // Plain decomposition / composition.
 struct NoEpi {
-  static constexpr bool kWeightIn = false, kNormOut = false;
+  static constexpr bool kWeightIn = false, kNormOut = false, kMirror = false;
 };
 // Composition of weighted coefficients: each loaded c_n is multiplied by g w_n first.
 struct WeightInEpi {
-  static constexpr bool kWeightIn = true, kNormOut = false;
+  static constexpr bool kWeightIn = true, kNormOut = false, kMirror = false;
 };
 // Decomposition that also accumulates sum_n w_n |c_n|^2 over the coefficients it stores.
 struct NormOutEpi {
-  static constexpr bool kWeightIn = false, kNormOut = true;
+  static constexpr bool kWeightIn = false, kNormOut = true, kMirror = false;
+};
+// Decomposition of a Hermitian G from its upper triangle: an element G[r, r ^ x] below the
+// diagonal (bit h of r set, h the top set bit of x) is read as conj(G[r ^ x, r]).
+struct MirrorUpperEpi {
+  static constexpr bool kWeightIn = false, kNormOut = false, kMirror = true;
 };
 
 // Per-thread accumulator of w_n |c_n|^2: FP64 for complex128; for complex64 a TwoSum-compensated
@@ -542,8 +551,23 @@ __device__ __forceinline__ double run_unit(const void* __restrict__ in, void* __
   ain.init(base, x, y0);
   typename AR::Raw raw[E];
   uint32_t emax = 0;
+  if constexpr (EPI::kMirror) {
+    static_assert(!COMPOSE, "mirrored reads are for the decomposition");
+    const uint32_t h = x ? 31u - (uint32_t)__clz(x) : 32u;
 #pragma unroll
-  for (int j = 0; j < E; ++j) raw[j] = AR::load(in, ain.at(LY::reg_u(0, j) >> K));
+    for (int j = 0; j < E; ++j) {
+      const uint32_t r = y0 | (LY::reg_u(0, j) >> K);
+      const bool lower = h < 32u && ((r >> h) & 1u);
+      const unsigned long long i =
+          lower ? base + ((unsigned long long)(r ^ x) << N) + r : ain.at(LY::reg_u(0, j) >> K);
+      raw[j] = AR::load(in, i);
+      if (lower) raw[j] = AR::conj(raw[j]);
+      if (x == 0u) raw[j] = AR::real_part(raw[j]);  // the diagonal: its imaginary parts are not used
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < E; ++j) raw[j] = AR::load(in, ain.at(LY::reg_u(0, j) >> K));
+  }
   if constexpr (EPI::kWeightIn) {
     const Real* w = static_cast<const Real*>(ea.w);
     const Real g = ea.g ? *static_cast<const Real*>(ea.g) : Real(1);
@@ -611,6 +635,97 @@ __device__ __forceinline__ void unit_prefetch(const void* in, unsigned long long
   an.init(base, xb | (t & ((1u << K) - 1u)), LY::thread_u(0, t) >> K);
 #pragma unroll
   for (int j = 0; j < LY::E; ++j) AR::prefetch(in, an.at(LY::reg_u(0, j) >> K));
+}
+
+// ----------------------------------------------- Hermitian G from its upper triangle --
+// For a Hermitian G the XOR-diagonal of a class x != 0 satisfies e_x[r ^ x] = conj(e_x[r]).
+// With h the top set bit of x, pair each row r having r_h = 0 with r ^ x (which has bit h set;
+// r < r ^ x, so e_x[r] = G[r, r ^ x] lies above the diagonal). Then for every z
+//   W_x[z] = sum_{r_h = 0} (-1)^popc(r & z) (e_x[r] + (-1)^popc(x & z) conj(e_x[r])),
+// and with V[z'] the WHT over the N - 1 bits other than h of e_x restricted to r_h = 0
+// (z' = z without bit h) this gives, for both z with that z',
+//   c(x, z) = 2^-N i^popc(x&z) W_x[z] = 2^(1-N) Re(V[z'] i^popc(x&z)).
+// So a unit reads only the upper triangle (half of G), transforms 2^(N-1) rows per class with
+// the same machinery, and each transformed value gives two real coefficients: z0 (z_h = 0)
+// and z1 = z0 | 2^h, whose phases differ by one factor i. The classes [xb, xb + 2^K) of a unit
+// must share their top bit: xb >= 2^K. AR stores real parts (ReOut<...>).
+template <int UB, int RB, int N, class AR, class Prefetch>
+__device__ __forceinline__ void run_unit_herm(const void* __restrict__ in, void* __restrict__ out,
+                                              unsigned long long base, uint32_t xb, uint32_t xaddr, uint32_t* smax,
+                                              uint32_t t, Prefetch prefetch) {
+  constexpr int NH = N - 1;  // transformed row bits
+  using LY = Layout<UB, NH, RB>;
+  constexpr int K = LY::K;
+  constexpr int E = LY::E;
+  constexpr int LAST = LY::NPH - 1;
+  constexpr int LPRE = N < 9 ? 9 - N : 0;
+  const uint32_t c = t & ((1u << K) - 1u);
+  const uint32_t x = xb | c;
+  const uint32_t h = 31u - (uint32_t)__clz(xb);  // top bit of every class of the unit
+  const uint32_t lowm = (1u << h) - 1u;
+  // insert a zero at bit h: r' (N - 1 bits) -> r
+  auto ins = [&](uint32_t v) { return (v & lowm) | ((v & ~lowm) << 1); };
+  const uint32_t y0 = LY::thread_u(0, t) >> K;
+  const uint32_t yl = LY::thread_u(LAST, t) >> K;
+  const uint32_t r0 = ins(y0);
+  typename AR::Raw raw[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const uint32_t r = r0 | ins(LY::reg_u(0, j) >> K);
+    raw[j] = AR::load(in, base + ((unsigned long long)r << N) + (r ^ x));
+  }
+  prefetch();
+  uint32_t emax = 0;
+#pragma unroll
+  for (int j = 0; j < E; ++j) emax = max(emax, AR::exp_key(raw[j]));
+  uint32_t Ekey = 0;
+  if constexpr (AR::kScaled) {
+    if (t < (1u << K)) smax[t] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int m = 1 << K; m < 32; m <<= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, m));
+    if (((t & 31u) >> K) == 0) atomicMax(&smax[c], emax);
+    __syncthreads();
+    Ekey = smax[c];
+  }
+  // the class maximum over half the rows is the class maximum (the other half are conjugates)
+  const typename AR::Conv cv = AR::make_conv(N, Ekey, 1 - N);
+  typename AR::Elem v[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) v[j] = AR::template convert<LPRE>(raw[j], cv, 0u);
+  local_wht<LY, AR>(v, xaddr, t);
+  // outputs: z0 = ins(z'), z' = yl | (register part); n(x, z) = spread(x) ^ 3 spread(z) is
+  // linear in z, and inserting bit h moves the spread bits at and above 2h up by two
+  const uint32_t xc = (x & lowm) | ((x >> 1) & ~lowm);  // x without bit h, for popc(x & z0)
+  const uint32_t sm = spread_c(0xFFFFu) & ((1u << (2 * h)) - 1u);
+  auto ins3s = [&](uint32_t sp) { return 3u * ((sp & sm) | ((sp & ~sm) << 2)); };
+  const unsigned long long tb = base + (unsigned long long)(spread16(x) ^ ins3s(spread16(yl)));
+  const uint32_t flip = 3u << (2 * h);
+  BitSum<LY::regrow(LAST, 0), LY::regrow(LAST, 1), LY::regrow(LAST, 2), LY::regrow(LAST, 3)> xo;
+  xo.init(xc);
+  const uint32_t ko = (uint32_t)__popc(xc & yl);
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const unsigned long long n0 = tb ^ ins3s(spread_c(LY::reg_u(LAST, j) >> K));
+    const uint32_t k0 = ko + xo.at(j);
+    AR::store(out, n0, v[j], cv, k0);
+    AR::store(out, n0 ^ flip, v[j], cv, k0 + 1u);
+  }
+}
+
+template <int UB, int RB, int N, class AR>
+__device__ __forceinline__ void herm_prefetch(const void* in, unsigned long long base, uint32_t xb, uint32_t t) {
+  using LY = Layout<UB, N - 1, RB>;
+  constexpr int K = LY::K;
+  const uint32_t x = xb | (t & ((1u << K) - 1u));
+  const uint32_t lowm = (1u << (31u - (uint32_t)__clz(xb))) - 1u;
+  auto ins = [&](uint32_t v) { return (v & lowm) | ((v & ~lowm) << 1); };
+  const uint32_t r0 = ins(LY::thread_u(0, t) >> K);
+#pragma unroll
+  for (int j = 0; j < LY::E; ++j) {
+    const uint32_t r = r0 | ins(LY::reg_u(0, j) >> K);
+    AR::prefetch(in, base + ((unsigned long long)r << N) + (r ^ x));
+  }
 }
 
 }  // namespace xd

@@ -102,3 +102,61 @@ def test_hermitian_rejects_bad_output():
         pg.decompose_hermitian(G, out=torch.empty(256, dtype=torch.float32, device="cuda"))
     with pytest.raises(pg.PauliError):
         pg.decompose_hermitian(G, out=G.view(torch.float64).view(-1)[:256])
+
+
+# ------------------------------------------------------ Hermitian G from its upper triangle --
+def _from_upper(G):
+    """The Hermitian matrix with G's strict upper triangle and the real parts of its diagonal."""
+    U = np.triu(G, 1)
+    return U + U.conj().T + np.diag(np.diag(G).real)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("N", [1, 3, 5, 6, 7, 8, 10, 12])
+def test_upper_matches_oracle_and_full_read(N, dtype):
+    G = workloads.hermitian_complex(N, 1700 + N).astype(NP[dtype])
+    Gd = _dev(G)
+    got = pg.decompose_hermitian(Gd, upper=True).cpu().numpy()
+    _check_against_oracle(G, got, N, dtype, k=None if N <= 8 else 2048)
+    full = pg.decompose_hermitian(Gd).cpu().numpy()
+    assert np.max(np.abs(got.astype(np.float64) - full)) <= TOL[dtype] * np.max(np.abs(G))
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("N", [4, 7, 9, 12])
+def test_upper_never_reads_the_lower_triangle(N, dtype):
+    """NaN below the diagonal and in the diagonal's imaginary parts change nothing: the result
+    is bit for bit that of the Hermitian matrix."""
+    G = workloads.hermitian_complex(N, 1720 + N).astype(NP[dtype])
+    bad = G.copy()
+    low = np.tril_indices(1 << N, -1)
+    bad[low] = np.nan
+    d = np.diag_indices(1 << N)
+    bad.imag[d] = np.where(np.arange(1 << N) % 2 == 0, np.nan, 7.0)
+    assert np.all(np.isfinite(bad.real[d]))
+    a = pg.decompose_hermitian(_dev(G), upper=True).cpu().numpy()
+    b = pg.decompose_hermitian(_dev(bad), upper=True).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    assert np.all(np.isfinite(b))
+
+
+def test_upper_of_general_matrix_and_batch_and_plain():
+    """A non-Hermitian G gives the coefficients of the Hermitian matrix made from its upper
+    triangle; batches; the plain method with mirrored reads agrees."""
+    N, count = 9, 3
+    G = np.stack([workloads.gaussian_complex(N, 1740 + k) for k in range(count)])
+    Gd = _dev(G)
+    got = pg.decompose_hermitian(Gd, upper=True).cpu().numpy()
+    for k in range(count):
+        _check_against_oracle(_from_upper(G[k]), got[k], N, torch.complex128, k=1024)
+    plain = pg.decompose_hermitian(Gd[:1], upper=True, method="plain").cpu().numpy()
+    assert np.max(np.abs(plain[0] - got[0])) <= 1e-12 * np.max(np.abs(G[0]))
+
+
+def test_upper_rejects_unsupported_sizes():
+    G6 = _dev(workloads.hermitian_complex(6, 1750))
+    with pytest.raises(pg.PauliError):
+        pg.decompose_hermitian(G6, upper=True, method="xordiag")
+    G13 = torch.zeros(1 << 13, 1 << 13, dtype=torch.complex64, device="cuda")
+    with pytest.raises(pg.PauliError):
+        pg.decompose_hermitian(G13, upper=True)
