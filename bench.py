@@ -513,8 +513,26 @@ def batched_forms(pg, workloads, dev, oracle, timed, forms):
                 pg.decompose(g, out=o, method="plain")
 
         ms_sep = timed(separate, 1)
+        # the same batch as Hermitian matrices: upper triangles in, real coefficients out
+        rdt = torch.float64 if tdt == torch.complex128 else torch.float32
+        routs = [torch.empty(4 ** n, dtype=rdt, device=dev) for n in Ns]
+        hplan = pg.PauliPlan(Ns, dtype=tdt, hermitian=True)
+        hplan.bind(Gd, routs)
+        ms_herm = timed(hplan.graph_launch, 20)
+        herm_status = hplan.status()
+        herm_err = 0.0
+        for G, o, sl in zip(mats, routs, sel):
+            Gr = G.astype(npdt).astype(np.complex128)
+            got = o.cpu().numpy()[sl].astype(np.float64)
+            herm_err = max(herm_err, float(np.max(np.abs(got - oracle.decompose_at(Gr, sl.astype(np.uint64)).real))
+                                           / np.max(np.abs(Gr))))
+        hplan.close()
+        del routs
         forms[f"batched512_hermitian_{dname}"] = {
             "plan_graph_ms": ms_plan, "plan_coeffs_per_s": ncoef / (ms_plan * 1e-3), "plan_status": status,
+            "hermitian_plan_graph_ms": ms_herm, "hermitian_plan_coeffs_per_s": ncoef / (ms_herm * 1e-3),
+            "hermitian_plan_status": herm_status, "hermitian_plan_max_err_rel": herm_err,
+            "hermitian_plan_speedup_vs_plain": ms_sep / ms_herm,
             "separate_plain_ms": ms_sep, "separate_plain_coeffs_per_s": ncoef / (ms_sep * 1e-3),
             "speedup_vs_plain": ms_sep / ms_plan, "max_err_rel": float(max(errs)),
             "sample": "8 seeded coefficients per matrix vs the oracle"}

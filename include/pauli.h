@@ -201,6 +201,14 @@ typedef struct pauli_plan pauli_plan;
 
 int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
                       pauli_plan** plan);
+/* A plan for Hermitian matrices: each execution decomposes the bound matrices read from their
+ * upper triangle (as pauli_decompose_hermitian_upper: the strict lower triangle and the
+ * diagonal's imaginary parts are never used) and stores real coefficients, out_list[b] holding
+ * 4^N reals (double for PAULI_C128, float for PAULI_C64). Matrices from N = 7 (N = 6 with
+ * threads_per_block = 256) are cut into upper-triangle units over half the rows; smaller ones
+ * are one item each. Everything else as for pauli_plan_create. */
+int pauli_plan_create_hermitian(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
+                                pauli_plan** plan);
 int pauli_plan_bind(pauli_plan* plan, const void* const* G_list, void* const* out_list);
 int pauli_plan_execute(pauli_plan* plan, void* stream);
 int pauli_plan_graph_launch(pauli_plan* plan, void* stream);

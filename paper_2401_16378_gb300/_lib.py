@@ -36,6 +36,7 @@ SIGNATURES = {
     "pauli_decompose_host": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp]),
     "pauli_decompose_batch_static": (_i, [_vpp, _ip, _i, _i, _vpp, _vp]),
     "pauli_plan_create": (_i, [_ip, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_void_p)]),
+    "pauli_plan_create_hermitian": (_i, [_ip, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_void_p)]),
     "pauli_plan_bind": (_i, [_vp, _vpp, _vpp]),
     "pauli_plan_execute": (_i, [_vp, _vp]),
     "pauli_plan_graph_launch": (_i, [_vp, _vp]),

@@ -266,18 +266,21 @@ class PauliPlan:
     """One persistent launch decomposing a batch of matrices of uneven N (pauli_plan_*)."""
 
     def __init__(self, Ns: Sequence[int], dtype: torch.dtype = torch.complex128, threads_per_block: int = 0,
-                 blocks_per_sm: int = 0):
+                 blocks_per_sm: int = 0, hermitian: bool = False):
+        """hermitian=True: the matrices are Hermitian, read from their upper triangle; outputs
+        are real tensors of 4^N values (pauli_plan_create_hermitian)."""
         self._lib = _lib.load()
         self.Ns = [int(n) for n in Ns]
         self.dtype = dtype
+        self.hermitian = bool(hermitian)
         if not threads_per_block:  # the autotuned CTA size on this GPU model, if measured
             from . import autotune
 
             threads_per_block = autotune.plan_threads(dtype)
         narr = (ctypes.c_int * len(self.Ns))(*self.Ns)
         h = ctypes.c_void_p()
-        check(self._lib.pauli_plan_create(narr, len(self.Ns), _DTYPES[dtype], int(threads_per_block),
-                                          int(blocks_per_sm), ctypes.byref(h)))
+        create = self._lib.pauli_plan_create_hermitian if self.hermitian else self._lib.pauli_plan_create
+        check(create(narr, len(self.Ns), _DTYPES[dtype], int(threads_per_block), int(blocks_per_sm), ctypes.byref(h)))
         self._h = h
         self._bound = None
 

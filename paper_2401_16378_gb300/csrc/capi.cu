@@ -89,6 +89,25 @@ int check_pair(const void* in, const char* in_name, int N, long long count, int 
   return PAULI_OK;
 }
 
+// Validates a (matrix batch -> real coefficient batch) pair: count * 4^N complex inputs and as
+// many reals out.
+int check_real_out(const void* G, int N, long long count, int dtype, const void* out_re) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (count < 1) return fail(PAULI_ERR_ARG, "count = %lld must be >= 1", count);
+  if (!G) return fail(PAULI_ERR_NULL, "G is NULL");
+  if (!out_re) return fail(PAULI_ERR_NULL, "out_re is NULL");
+  const size_t es = elem_bytes(dtype);
+  if ((st = check_aligned(G, es, "G"))) return st;
+  if ((st = check_aligned(out_re, es / 2, "out_re"))) return st;
+  const unsigned long long per = 1ull << (2 * N);
+  if ((unsigned long long)count > (~0ull / es) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
+  const size_t in_bytes = (size_t)(per * (unsigned long long)count) * es;
+  if (overlaps(G, in_bytes, out_re, in_bytes / 2)) return fail(PAULI_ERR_ALIAS, "G and out_re overlap");
+  return PAULI_OK;
+}
+
 int resolve_method(int method, int N, int* out) {
   if (method == PAULI_AUTO) {
     *out = pauli::xordiag_supported(N) ? PAULI_XORDIAG : PAULI_PLAIN;
@@ -137,19 +156,8 @@ int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int m
 }
 
 int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* out_re, int method, void* stream) {
-  int st;
-  if ((st = check_dtype(dtype))) return st;
-  if ((st = check_n(N))) return st;
-  if (count < 1) return fail(PAULI_ERR_ARG, "count = %d must be >= 1", count);
-  if (!G) return fail(PAULI_ERR_NULL, "G is NULL");
-  if (!out_re) return fail(PAULI_ERR_NULL, "out_re is NULL");
-  const size_t es = elem_bytes(dtype);
-  if ((st = check_aligned(G, es, "G"))) return st;
-  if ((st = check_aligned(out_re, es / 2, "out_re"))) return st;
-  const unsigned long long per = 1ull << (2 * N);
-  if ((unsigned long long)count > (~0ull / es) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
-  const size_t in_bytes = (size_t)(per * (unsigned long long)count) * es;
-  if (overlaps(G, in_bytes, out_re, in_bytes / 2)) return fail(PAULI_ERR_ALIAS, "G and out_re overlap");
+  int st = check_real_out(G, N, count, dtype, out_re);
+  if (st) return st;
   int m = 0;
   if ((st = resolve_method(method, N, &m))) return st;
   if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
@@ -162,19 +170,8 @@ int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* 
 
 int pauli_decompose_hermitian_upper(const void* G, int N, int count, int dtype, void* out_re, int method,
                                     void* stream) {
-  int st;
-  if ((st = check_dtype(dtype))) return st;
-  if ((st = check_n(N))) return st;
-  if (count < 1) return fail(PAULI_ERR_ARG, "count = %d must be >= 1", count);
-  if (!G) return fail(PAULI_ERR_NULL, "G is NULL");
-  if (!out_re) return fail(PAULI_ERR_NULL, "out_re is NULL");
-  const size_t es = elem_bytes(dtype);
-  if ((st = check_aligned(G, es, "G"))) return st;
-  if ((st = check_aligned(out_re, es / 2, "out_re"))) return st;
-  const unsigned long long per = 1ull << (2 * N);
-  if ((unsigned long long)count > (~0ull / es) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
-  const size_t in_bytes = (size_t)(per * (unsigned long long)count) * es;
-  if (overlaps(G, in_bytes, out_re, in_bytes / 2)) return fail(PAULI_ERR_ALIAS, "G and out_re overlap");
+  int st = check_real_out(G, N, count, dtype, out_re);
+  if (st) return st;
   if (method != PAULI_AUTO && method != PAULI_PLAIN && method != PAULI_XORDIAG)
     return fail(PAULI_ERR_ARG, "method %d is not a pauli_method", method);
   if (N > 12) return fail(PAULI_ERR_UNSUPPORTED, "pauli_decompose_hermitian_upper is built for N <= 12, not N = %d", N);
@@ -404,6 +401,7 @@ int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* 
 // ------------------------------------------------------------------------------ plans --
 struct pauli_plan {
   std::vector<int> Ns;
+  bool herm = false;  // Hermitian matrices read from the upper triangle, real outputs
   int dtype = PAULI_C128;
   int UB = 13;
   int blocks_per_sm = 0;
@@ -433,17 +431,13 @@ int plan_enqueue(pauli_plan* p, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(int), s);  // counter, status
   if (e != cudaSuccess) return cuda_fail(e, "plan reset");
   e = pauli::launch_plan(p->d_items, p->n_items, p->d_mats, p->d_ctrl, p->dtype == PAULI_C64, p->UB, p->blocks_per_sm,
-                         s);
+                         s, 0, p->herm);
   if (e != cudaSuccess) return cuda_fail(e, "plan launch");
   return PAULI_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
-                      pauli_plan** plan) {
+int plan_create(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm, bool herm,
+                pauli_plan** plan) {
   int st;
   if (!plan) return fail(PAULI_ERR_NULL, "plan is NULL");
   *plan = nullptr;
@@ -458,18 +452,17 @@ int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_b
   pauli_plan* p = new (std::nothrow) pauli_plan;
   if (!p) return fail(PAULI_ERR_NOMEM, "plan allocation failed");
   p->Ns.assign(N_list, N_list + batch);
+  p->herm = herm;
   p->dtype = dtype;
   p->UB = threads_per_block == 256 ? 12 : 13;
   p->blocks_per_sm = blocks_per_sm;
   // work list: one item per unit (or per small matrix), largest N first
   std::vector<pauli::PlanItem> items;
-  const int nmin = pauli::plan_min_unit_n(p->UB);
   std::vector<int> order(batch);
   for (int b = 0; b < batch; ++b) order[b] = b;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return N_list[a] > N_list[b]; });
   for (int b : order) {
-    const int N = N_list[b];
-    const unsigned units = N >= nmin ? (unsigned)((1ull << (2 * N)) >> p->UB) : 1u;
+    const unsigned units = pauli::plan_units(N_list[b], p->UB, herm);
     for (unsigned u = 0; u < units; ++u) items.push_back(pauli::PlanItem{(uint32_t)b, u});
   }
   p->n_items = (int)items.size();
@@ -491,12 +484,27 @@ int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_b
   return PAULI_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int pauli_plan_create(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
+                      pauli_plan** plan) {
+  return plan_create(N_list, batch, dtype, threads_per_block, blocks_per_sm, false, plan);
+}
+
+int pauli_plan_create_hermitian(const int* N_list, int batch, int dtype, int threads_per_block, int blocks_per_sm,
+                                pauli_plan** plan) {
+  return plan_create(N_list, batch, dtype, threads_per_block, blocks_per_sm, true, plan);
+}
+
 int pauli_plan_bind(pauli_plan* p, const void* const* G_list, void* const* out_list) {
   if (!p) return fail(PAULI_ERR_NULL, "plan is NULL");
   if (!G_list || !out_list) return fail(PAULI_ERR_NULL, "G_list and out_list must not be NULL");
   std::vector<pauli::PlanMat> mats(p->Ns.size());
   for (size_t b = 0; b < p->Ns.size(); ++b) {
-    int st = check_pair(G_list[b], "G_list[b]", p->Ns[b], 1, p->dtype, out_list[b], "out_list[b]");
+    int st = p->herm ? check_real_out(G_list[b], p->Ns[b], 1, p->dtype, out_list[b])
+                     : check_pair(G_list[b], "G_list[b]", p->Ns[b], 1, p->dtype, out_list[b], "out_list[b]");
     if (st) return fail(st, "entry %zu: %s", b, g_err.c_str());
     mats[b] = pauli::PlanMat{G_list[b], out_list[b], p->Ns[b], 0};  // items list in use: first unused
   }

@@ -1,0 +1,12 @@
+// plan_herm_u12_c128.cu -- Hermitian plan kernel instantiation: 256-thread CTAs, c128,
+// matrices read from their upper triangle, real coefficients.
+#include "plan_kernels.cuh"
+
+namespace pauli {
+
+cudaError_t plan_herm_u12_c128(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl,
+                                int blocks_per_sm, cudaStream_t s, int batch) {
+  return pk::launch_plan_t<12, xd::ReOut<xd::ArC128>, true>(items, n_items, mats, ctrl, blocks_per_sm, s, batch);
+}
+
+}  // namespace pauli

@@ -20,7 +20,9 @@ static constexpr int kStallPolls = 1 << 17;  // ~0.1-1 s of polling before the w
 
 // Whole N-qubit matrix (N <= 6) in one CTA: elements u = class | (row << N) in shared memory,
 // per-class fixed-point scale, N butterfly stages in shared memory, phase and store.
-template <int N, class AR>
+// MIRROR: G is Hermitian and read from its upper triangle (an element below the diagonal is
+// read as the conjugate of its mirror, the diagonal's imaginary parts are dropped).
+template <int N, class AR, bool MIRROR = false>
 __device__ void run_small(const void* __restrict__ in, void* __restrict__ out, uint32_t xaddr, uint32_t* smax,
                           uint32_t t, uint32_t T) {
   constexpr uint32_t D = 1u << N, E = D * D;
@@ -31,7 +33,18 @@ __device__ void run_small(const void* __restrict__ in, void* __restrict__ out, u
   }
   for (uint32_t u = t; u < E; u += T) {
     const uint32_t c = u & (D - 1u), r = u >> N;
-    const typename AR::Raw raw = AR::load(in, (unsigned long long)r * D + (r ^ c));
+    typename AR::Raw raw;
+    if constexpr (MIRROR) {
+      const bool lower = c && ((r >> (31u - (uint32_t)__clz(c))) & 1u);
+      if (lower) {
+        raw = AR::conj(AR::load(in, (unsigned long long)(r ^ c) * D + r));
+      } else {
+        raw = AR::load(in, (unsigned long long)r * D + (r ^ c));
+        if (c == 0u) raw = AR::real_part(raw);
+      }
+    } else {
+      raw = AR::load(in, (unsigned long long)r * D + (r ^ c));
+    }
     if (AR::kScaled) atomicMax(&smax[c], AR::exp_key(raw));
     sts128(xaddr + 16u * u, AR::raw_pack(raw));
   }
@@ -60,18 +73,24 @@ __device__ void run_small(const void* __restrict__ in, void* __restrict__ out, u
   }
 }
 
-// L2 prefetch of every input row segment of item `it` (128-byte lines).
+// L2 prefetch of every input row segment of item `it` (128-byte lines). HERM: the item's rows
+// are those with bit h of the unit's classes clear (upper-triangle units, unit > 0).
 __device__ __forceinline__ void prefetch_item(const PlanItem& it, const PlanMat& m, int UB, size_t esz, uint32_t t,
-                                              uint32_t T) {
+                                              uint32_t T, bool herm = false) {
   const uint32_t D = 1u << m.N;
-  const int small = m.N < plan_min_unit_n(UB);
-  const int K = small ? m.N : UB - m.N;
+  const int nmin = herm ? plan_min_herm_n(UB) : plan_min_unit_n(UB);
+  const int small = m.N < nmin;
+  const bool half = herm && !small && it.unit > 0;
+  const int K = small ? m.N : UB - m.N + (half ? 1 : 0);
   const uint32_t seg = (1u << K) * (uint32_t)esz;  // bytes of the unit's classes in one row
   const uint32_t lines = seg > 128u ? seg / 128u : 1u;
-  const uint32_t xb = small ? 0u : it.unit << K;
+  const uint32_t xb = small ? 0u : it.unit << (UB - m.N + (herm ? 1 : 0));
+  const uint32_t lowm = half ? (1u << (31u - (uint32_t)__clz(xb))) - 1u : ~0u;
+  const uint32_t rows = half ? D / 2 : D;
   const char* base = reinterpret_cast<const char*>(m.in);
-  for (uint32_t i = t; i < D * lines; i += T) {
-    const uint32_t r = i / lines, l = i % lines;
+  for (uint32_t i = t; i < rows * lines; i += T) {
+    const uint32_t rr = i / lines, l = i % lines;
+    const uint32_t r = half ? ((rr & lowm) | ((rr & ~lowm) << 1)) : rr;
     const unsigned long long col = (r ^ xb) & ~((1u << K) - 1u);
     asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((unsigned long long)r * D + col) * esz + 128ull * l));
   }
@@ -91,12 +110,55 @@ __device__ __forceinline__ PlanItem item_from_table(int cur, const PlanMat* __re
   return PlanItem{(uint32_t)lo, (uint32_t)(cur - mats[lo].first)};
 }
 
-template <int UB, class AR>
+// One work unit of an N-qubit matrix (N >= the unit threshold). The Hermitian form is kept out
+// of line: each N's body is compiled once, which keeps the build of the kernel short.
+template <int UB, int N, class AR, bool HERM, class Prefetch>
+__device__ __forceinline__ void plan_unit_inl(const PlanMat& m, uint32_t unit, uint32_t xaddr, uint32_t* smax, uint32_t t,
+                                          Prefetch pf) {
+  if constexpr (!HERM) {
+    run_unit<UB, 4, N, AR, false>(m.in, m.out, 0ull, unit << (UB - N), 0, xaddr, smax, t, pf);
+  } else if constexpr (2 * N <= UB) {
+    // an upper-triangle unit would hold more classes than the matrix has: one full-row unit
+    // holds the whole matrix (N = 6 with 4096-element units)
+    run_unit<UB, 4, N, AR, false, Prefetch, MirrorUpperEpi>(m.in, m.out, 0ull, 0u, 0, xaddr, smax, t, pf);
+  } else {
+    constexpr int KH = UB - N + 1, KR = UB - N;
+    if (unit == 0) {
+#pragma unroll 1
+      for (uint32_t q = 0; q < 2u; ++q) {
+        run_unit<UB, 4, N, AR, false, Prefetch, MirrorUpperEpi>(m.in, m.out, 0ull, q << KR, 0, xaddr, smax, t, pf);
+        __syncthreads();
+      }
+    } else {
+      run_unit_herm<UB, 4, N, AR>(m.in, m.out, 0ull, unit << KH, xaddr, smax, t, pf);
+    }
+  }
+}
+
+template <int UB, int N, class AR, bool HERM, class Prefetch>
+__device__ __noinline__ void plan_unit_call(const PlanMat& m, uint32_t unit, uint32_t xaddr, uint32_t* smax, uint32_t t,
+                                            Prefetch pf) {
+  plan_unit_inl<UB, N, AR, HERM>(m, unit, xaddr, smax, t, pf);
+}
+template <int UB, int N, class AR, bool HERM, class Prefetch>
+__device__ __forceinline__ void plan_unit(const PlanMat& m, uint32_t unit, uint32_t xaddr, uint32_t* smax, uint32_t t,
+                                          Prefetch pf) {
+  if constexpr (HERM)
+    plan_unit_call<UB, N, AR, HERM>(m, unit, xaddr, smax, t, pf);
+  else
+    plan_unit_inl<UB, N, AR, HERM>(m, unit, xaddr, smax, t, pf);
+}
+
+// HERM: every matrix is Hermitian and read from its upper triangle; AR stores real parts.
+// Matrices from N = plan_min_herm_n(UB) on are cut into units of 2^(UB - N + 1) classes over
+// half the rows (run_unit_herm); unit 0 (the diagonal and classes below 2^(UB - N + 1), of
+// different top bits) runs as two full-row units with the lower triangle mirrored.
+template <int UB, class AR, bool HERM = false>
 __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlocks))
     plan_kernel(const PlanItem* __restrict__ items, int n_items, const PlanMat* __restrict__ mats, PlanCtrl* ctrl,
                 int batch) {
   extern __shared__ __align__(16) uint4 xbuf[];
-  __shared__ uint32_t smax[64];
+  __shared__ uint32_t smax[128];
   __shared__ int s_next;
   const uint32_t t = threadIdx.x, T = blockDim.x;
   const uint32_t xaddr = (uint32_t)__cvta_generic_to_shared(xbuf);
@@ -123,14 +185,14 @@ __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlo
     auto pf = [&]() {
       if (nxt < n_items) {
         const PlanItem in2 = items ? items[nxt] : item_from_table(nxt, mats, batch);
-        prefetch_item(in2, mats[in2.mat], UB, esz, t, T);
+        prefetch_item(in2, mats[in2.mat], UB, esz, t, T, HERM);
       }
     };
-#define PLAN_UNIT(NQ) run_unit<UB, 4, NQ, AR, false>(m.in, m.out, 0ull, it.unit << (UB - NQ), 0, xaddr, smax, t, pf)
+#define PLAN_UNIT(NQ) plan_unit<UB, NQ, AR, HERM>(m, it.unit, xaddr, smax, t, pf)
 #define PLAN_SMALL(NQ) \
   do {                 \
     pf();              \
-    run_small<NQ, AR>(m.in, m.out, xaddr, smax, t, T); \
+    run_small<NQ, AR, HERM>(m.in, m.out, xaddr, smax, t, T); \
   } while (0)
     switch (m.N) {
       case 1: PLAN_SMALL(1); break;
@@ -153,10 +215,10 @@ __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlo
   }
 }
 
-template <int UB, class AR>
+template <int UB, class AR, bool HERM = false>
 cudaError_t launch_plan_t(const PlanItem* items, int n_items, const PlanMat* mats, PlanCtrl* ctrl, int blocks_per_sm,
                           cudaStream_t s, int batch = 0) {
-  auto kern = plan_kernel<UB, AR>;
+  auto kern = plan_kernel<UB, AR, HERM>;
   constexpr size_t smem = Unit<UB, 4>::kSmem;
   static int resident = 0;
   if (!resident) {
