@@ -173,6 +173,22 @@ int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch
 int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* out_host, void* G_dev,
                          void* out_dev, int method, void* stream);
 
+/* Streams a list of host matrices of one N through the device: matrix k is copied in from
+ * G_host_list[k], decomposed (method as for pauli_decompose) and its 4^N coefficients copied out
+ * to out_host_list[k]. The work is pipelined over two caller-owned device buffer pairs
+ * (G_dev[0..1], out_dev[0..1]: device arrays of 4^N elements each, all four distinct) and three
+ * library streams -- copy in, compute, copy out -- ordered by events, so that the copy-in of
+ * matrix k + 1, the decomposition of matrix k and the copy-out of matrix k - 1 proceed at once
+ * (both directions of the host link and the SMs busy together). The pipeline starts after
+ * earlier work on `stream`, and later work on `stream` waits for its last copy; the call
+ * returns after enqueueing. Host buffers should be pinned (else the copies are synchronous)
+ * and stay valid until the stream has finished. G_host_list, out_host_list: host arrays of
+ * n_mats host pointers (an input may repeat); G_dev, out_dev: host arrays of 2 device pointers.
+ * The library's streams and events are created at the first call on each device and kept;
+ * calls on one device enqueue one at a time. */
+int pauli_decompose_host_stream(const void* const* G_host_list, void* const* out_host_list, int n_mats, int N,
+                                int dtype, void* const* G_dev, void* const* out_dev, int method, void* stream);
+
 /* Batched decomposition for callers that cannot allocate device memory (a fixed memory
  * budget, an allocator that must not be re-entered, ...). Same result and same one-launch
  * schedule as a plan over N_list, but the library allocates nothing: the work counter,

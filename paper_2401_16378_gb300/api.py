@@ -262,6 +262,32 @@ def pauli_decompose_host(G_host: torch.Tensor, out_host: torch.Tensor, G_dev: to
                                            G_dev.data_ptr(), out_dev.data_ptr(), _method(method), _stream(stream)))
 
 
+def pauli_decompose_host_stream(G_hosts: Sequence[torch.Tensor], out_hosts: Sequence[torch.Tensor],
+                                G_devs: Sequence[torch.Tensor], out_devs: Sequence[torch.Tensor], method="auto",
+                                stream=None) -> None:
+    """Decompose a list of host matrices of one N: copy-in, decomposition and copy-out pipelined
+    over the library's streams and the two device buffer pairs G_devs[0..1], out_devs[0..1]
+    (asynchronous; pinned host tensors; synchronise `stream` before reading out_hosts)."""
+    if len(G_hosts) != len(out_hosts) or not G_hosts:
+        raise ValueError("one output per input matrix, at least one")
+    if len(G_devs) != 2 or len(out_devs) != 2:
+        raise ValueError("two device input buffers and two device output buffers")
+    N = _qubits_of_matrix(G_hosts[0])
+    for t in list(G_hosts) + list(out_hosts):
+        if t.is_cuda or not t.is_contiguous() or t.numel() != 4 ** N or t.dtype != G_hosts[0].dtype:
+            raise ValueError("host buffers: contiguous, on the host, 4^N elements of one complex dtype")
+    for t in list(G_devs) + list(out_devs):
+        _device_tensor(t, "device buffer")
+        if t.numel() != 4 ** N or t.dtype != G_hosts[0].dtype:
+            raise ValueError("device buffers: 4^N elements of the host buffers' dtype")
+    gh, k1 = _ptr_array([t.data_ptr() for t in G_hosts])
+    oh, k2 = _ptr_array([t.data_ptr() for t in out_hosts])
+    gd, k3 = _ptr_array([t.data_ptr() for t in G_devs])
+    od, k4 = _ptr_array([t.data_ptr() for t in out_devs])
+    check(_lib.load().pauli_decompose_host_stream(gh, oh, len(G_hosts), N, _dtype(G_hosts[0]), gd, od, _method(method),
+                                                  _stream(stream)))
+
+
 class PauliPlan:
     """One persistent launch decomposing a batch of matrices of uneven N (pauli_plan_*)."""
 
@@ -430,6 +456,7 @@ compose = pauli_compose
 coeffs_at = pauli_coeffs_at
 decompose_list = pauli_decompose_list
 decompose_host = pauli_decompose_host
+decompose_host_stream = pauli_decompose_host_stream
 decompose_hermitian = pauli_decompose_hermitian
 weighted_norm = pauli_weighted_norm
 decompose_weighted_norm = pauli_decompose_weighted_norm

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -124,6 +125,39 @@ int resolve_method(int method, int N, int* out) {
     return PAULI_OK;
   }
   return fail(PAULI_ERR_ARG, "method %d is not a pauli_method", method);
+}
+
+// Library streams of pauli_decompose_host_stream, one set per device, kept for the process:
+// copy in, compute, copy out, and the events that order them. Calls on a device take the mutex
+// while they enqueue.
+struct HostPipe {
+  std::mutex mutex;
+  cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, end = nullptr, in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
+};
+std::mutex g_pipes_mutex;
+std::vector<std::pair<int, HostPipe*>> g_pipes;
+
+cudaError_t host_pipe(HostPipe** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_pipes_mutex);
+  for (auto& p : g_pipes)
+    if (p.first == dev) {
+      *out = p.second;
+      return cudaSuccess;
+    }
+  HostPipe* hp = new (std::nothrow) HostPipe;
+  if (!hp) return cudaErrorMemoryAllocation;
+  for (cudaStream_t* s : {&hp->in, &hp->comp, &hp->out})
+    if ((e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  for (cudaEvent_t* ev : {&hp->start, &hp->end, &hp->in_done[0], &hp->in_done[1], &hp->comp_done[0],
+                          &hp->comp_done[1], &hp->out_done[0], &hp->out_done[1]})
+    if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  g_pipes.emplace_back(dev, hp);
+  *out = hp;
+  return cudaSuccess;
 }
 
 int decompose_checked(const void* G, int N, long long count, int dtype, void* out, int method, cudaStream_t s) {
@@ -393,6 +427,61 @@ int pauli_decompose_host(const void* G_host, int N, int count, int dtype, void* 
   if ((st = decompose_checked(G_dev, N, count, dtype, out_dev, method, s))) return st;
   e = cudaMemcpyAsync(out_host, out_dev, bytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_host: copy to host");
+  return PAULI_OK;
+}
+
+int pauli_decompose_host_stream(const void* const* G_host_list, void* const* out_host_list, int n_mats, int N,
+                                int dtype, void* const* G_dev, void* const* out_dev, int method, void* stream) {
+  if (!G_host_list || !out_host_list) return fail(PAULI_ERR_NULL, "G_host_list and out_host_list must not be NULL");
+  if (!G_dev || !out_dev) return fail(PAULI_ERR_NULL, "G_dev and out_dev must not be NULL");
+  if (n_mats < 1) return fail(PAULI_ERR_ARG, "n_mats = %d must be >= 1", n_mats);
+  int st;
+  for (int b = 0; b < 2; ++b)
+    if ((st = check_pair(G_dev[b], "G_dev[b]", N, 1, dtype, out_dev[b], "out_dev[b]"))) return st;
+  const size_t bytes = (size_t)(1ull << (2 * N)) * elem_bytes(dtype);
+  const void* bufs[4] = {G_dev[0], G_dev[1], out_dev[0], out_dev[1]};
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j)
+      if (overlaps(bufs[i], bytes, bufs[j], bytes)) return fail(PAULI_ERR_ALIAS, "the four device buffers overlap");
+  for (int k = 0; k < n_mats; ++k) {
+    if (!G_host_list[k] || !out_host_list[k]) return fail(PAULI_ERR_NULL, "host buffer %d is NULL", k);
+    if (overlaps(G_host_list[k], bytes, out_host_list[k], bytes))
+      return fail(PAULI_ERR_ALIAS, "G_host_list[%d] and out_host_list[%d] overlap", k, k);
+  }
+  int m = 0;
+  if ((st = resolve_method(method, N, &m))) return st;
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  HostPipe* hp = nullptr;
+  cudaError_t e = host_pipe(&hp);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_host_stream: streams");
+  std::lock_guard<std::mutex> lock(hp->mutex);
+  const cudaStream_t user = (cudaStream_t)stream;
+  // the pipeline starts after earlier work on the caller's stream
+  if ((e = cudaEventRecord(hp->start, user)) != cudaSuccess) return cuda_fail(e, "pauli_decompose_host_stream");
+  for (cudaStream_t s : {hp->in, hp->comp, hp->out})
+    if ((e = cudaStreamWaitEvent(s, hp->start, 0)) != cudaSuccess) return cuda_fail(e, "pauli_decompose_host_stream");
+  for (int k = 0; k < n_mats; ++k) {
+    const int b = k & 1;
+    // copy in: buffer b is free once the decomposition of matrix k - 2 has read it
+    if (k >= 2 && (e = cudaStreamWaitEvent(hp->in, hp->comp_done[b], 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(G_dev[b], G_host_list[k], bytes, cudaMemcpyHostToDevice, hp->in)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(hp->in_done[b], hp->in)) != cudaSuccess) break;
+    // decompose: needs matrix k in, and out_dev[b] copied out for matrix k - 2
+    if ((e = cudaStreamWaitEvent(hp->comp, hp->in_done[b], 0)) != cudaSuccess) break;
+    if (k >= 2 && (e = cudaStreamWaitEvent(hp->comp, hp->out_done[b], 0)) != cudaSuccess) break;
+    if ((st = decompose_checked(G_dev[b], N, 1, dtype, out_dev[b], m, hp->comp))) return st;
+    if ((e = cudaEventRecord(hp->comp_done[b], hp->comp)) != cudaSuccess) break;
+    // copy out
+    if ((e = cudaStreamWaitEvent(hp->out, hp->comp_done[b], 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(out_host_list[k], out_dev[b], bytes, cudaMemcpyDeviceToHost, hp->out)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(hp->out_done[b], hp->out)) != cudaSuccess) break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_host_stream: enqueue");
+  // later work on the caller's stream waits for the last copy out (which follows everything else)
+  if ((e = cudaEventRecord(hp->end, hp->out)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(user, hp->end, 0)) != cudaSuccess)
+    return cuda_fail(e, "pauli_decompose_host_stream: join");
   return PAULI_OK;
 }
 

@@ -124,6 +124,17 @@ def test_hermitian_and_norm_reject_bad_arguments(lib):
     assert lib.pauli_compose_weighted(P(A), 4, 1, C128, P(B + 32), None, P(B), 0, None) == ALIAS
 
 
+def test_host_stream_rejects_bad_arguments(lib):
+    arr = lambda *v: (ctypes.c_void_p * len(v))(*[ctypes.c_void_p(x) for x in v])  # noqa: E731
+    hosts, outs = arr(A), arr(A + (1 << 20))
+    devs_g, devs_o = arr(B, B + 8192), arr(B + 16384, B + 24576)
+    assert lib.pauli_decompose_host_stream(None, outs, 1, 4, C128, devs_g, devs_o, 0, None) == NULL
+    assert lib.pauli_decompose_host_stream(hosts, outs, 0, 4, C128, devs_g, devs_o, 0, None) == ARG
+    assert lib.pauli_decompose_host_stream(hosts, outs, 1, 4, C128, arr(B, B + 16), devs_o, 0, None) == ALIAS
+    assert lib.pauli_decompose_host_stream(hosts, arr(A + 16), 1, 4, C128, devs_g, devs_o, 0, None) == ALIAS
+    assert lib.pauli_decompose_host_stream(hosts, outs, 1, 4, C128, devs_g, devs_o, 9, None) == ARG
+
+
 def test_coeffs_at_rejects_bad_arguments(lib):
     assert lib.pauli_coeffs_at(P(A), 4, C128, P(B), 0, P(B + 4096), None) == OK  # k = 0: nothing to do
     assert lib.pauli_coeffs_at(P(A), 4, C128, P(B), -1, P(B + 4096), None) == ARG
