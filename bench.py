@@ -415,6 +415,16 @@ def n6_form(pg, workloads, dev, oracle, timed, forms):
     ms6 = timed(lambda: pg.decompose(g6, out=o6, method="plain"), 50)
     err6 = float(np.max(np.abs(o6.cpu().numpy() - oracle.decompose_full(G6))) / np.max(np.abs(G6)))
     forms["n6_plain_c128"] = {"us_per_call": ms6 * 1e3, "coeffs_per_s": 4 ** 6 / (ms6 * 1e-3), "max_err_rel": err6}
+    # the complex64 path on the same input (TwoSum-compensated FP32), error against the FP64 oracle
+    # of the exactly upcast input
+    G6s = G6.astype(np.complex64)
+    g6s = torch.from_numpy(G6s).to(dev)
+    o6s = torch.empty(4 ** 6, dtype=torch.complex64, device=dev)
+    ms6s = timed(lambda: pg.decompose(g6s, out=o6s, method="plain"), 50)
+    want6s = oracle.decompose_full(G6s.astype(np.complex128))
+    forms["n6_plain_c64"] = {"us_per_call": ms6s * 1e3, "coeffs_per_s": 4 ** 6 / (ms6s * 1e-3),
+                             "max_err_rel": float(np.max(np.abs(o6s.cpu().numpy() - want6s)) / np.max(np.abs(G6s))),
+                             "tolerance_rel": 2e-6}
 
 
 def n12_forms(pg, workloads, dev, oracle, timed, forms):
@@ -454,7 +464,18 @@ def n12_forms(pg, workloads, dev, oracle, timed, forms):
                 "hbm_gbs_algorithmic": 4 ** N * (8 + 8) / (ms * 1e-3) / 1e9,
                 "reads": "diagonal and upper triangle of G only"}
             del r
-        del g, o
+        # the complex64 path on the same input, error against the FP64 oracle of the upcast input
+        Gs = G.astype(np.complex64)
+        gs = torch.from_numpy(Gs).to(dev)
+        os_ = torch.empty(4 ** N, dtype=torch.complex64, device=dev)
+        ms = timed(lambda: pg.decompose(gs, out=os_, method="xordiag"), 20)
+        want_s = oracle.decompose_at(Gs.astype(np.complex128), idx)
+        err = float(np.max(np.abs(os_.cpu().numpy()[idx.astype(np.int64)].astype(np.complex128) - want_s))
+                    / np.max(np.abs(Gs)))
+        forms[f"n12_{name}_xordiag_c64"] = {"ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3), "max_err_rel": err,
+                                            "hbm_gbs_algorithmic": 2 * 4 ** N * 8 / (ms * 1e-3) / 1e9,
+                                            "tolerance_rel": 2e-6}
+        del g, o, gs, os_
 
 
 def c64_form(pg, workloads, dev, oracle, timed, forms, G14):
@@ -592,7 +613,36 @@ def adjoint_form(pg, workloads, dev, oracle, timed, forms):
         "grad_max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(want))),
         "sample": "loss vs the oracle's norm of the 64 coefficient vectors; gradient of matrix 0 at 147 "
                   "entries vs the oracle's 2^-N compose of 2 w c"}
-    del Gt, A
+    del Gt
+    # the same step in complex64 (TwoSum-compensated FP32), errors against the FP64 oracle
+    A32 = A.astype(np.complex64)
+    w32_np = w_np.astype(np.float32)
+    w32 = torch.from_numpy(w32_np).to(dev)
+    Gs = torch.from_numpy(A32).to(dev).requires_grad_(True)
+
+    def step32():
+        Gs.grad = None
+        loss, c = pg.decompose_weighted_norm_autograd(Gs, w32)
+        loss.backward()
+        return c, loss
+
+    ms32 = timed(step32, 10)
+    c32, loss32 = step32()
+    torch.cuda.synchronize(dev)
+    c_ref = oracle.decompose_at(A32[0].astype(np.complex128), np.arange(4 ** N, dtype=np.uint64))
+    c_err = float(np.max(np.abs(c32[0].detach().cpu().numpy().astype(np.complex128) - c_ref)) / np.max(np.abs(A32[0])))
+    ch32 = c32.detach().cpu().numpy().astype(np.complex128)
+    want_loss32 = sum(oracle.weighted_norm(ch32[k], w32_np.astype(np.float64)) for k in range(B))
+    want32 = oracle.compose_at(oracle.weighted_norm_grad(ch32[0], w32_np.astype(np.float64)), rows, cols) * 2.0 ** -N
+    got32 = Gs.grad[0].cpu().numpy()[rows, cols].astype(np.complex128)
+    forms["adjoint64_n10_c64"] = {
+        "fwd_bwd_ms": ms32, "matrices_per_s": B / (ms32 * 1e-3),
+        "coeff_max_err_rel": c_err, "coeff_tolerance_rel": 2e-6,
+        "loss_err_rel": abs(float(loss32.detach().cpu()) - want_loss32) / want_loss32,
+        "grad_max_err_rel": float(np.max(np.abs(got32 - want32)) / np.max(np.abs(want32))),
+        "sample": "coefficients of matrix 0 (all) vs the FP64 oracle of the upcast input; loss vs the oracle's "
+                  "norm of the GPU coefficients; gradient of matrix 0 at 147 entries"}
+    del Gs, A
 
 
 def main():

@@ -92,6 +92,13 @@ def test_n12_config_both_methods(which):
     assert np.max(np.abs(cx - cp)) <= 2e-12 * maxabs(G)
     if which == "hermitian":
         assert np.max(np.abs(cx.imag)) <= 1e-12 * maxabs(G)
+        # the real-part and upper-triangle forms the bench times on the same input
+        re = host(pg.decompose_hermitian(Gd))
+        up = host(pg.decompose_hermitian(Gd, upper=True))
+        assert_close(re[i64], want.real, G, torch.complex128)
+        assert_close(up[i64], want.real, G, torch.complex128)
+        np.testing.assert_array_equal(re, cx.real)
+        assert np.max(np.abs(up - cx.real)) <= 2e-12 * maxabs(G)
 
 
 @pytest.mark.parametrize("method", ["plain", "xordiag"])
