@@ -38,7 +38,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--n", type=int, default=14, help="qubits of the timed workload")
+    p.add_argument("--n", "--qubits", dest="n", type=int, default=14, help="qubits of the timed workload")
     p.add_argument("--quick", action="store_true", help="skip the secondary forms")
     p.add_argument("--variant", default="default", choices=["default", "unit8192", "unit4096", "unit4096x8", "unit8192x8"],
                    help="XOR-diagonal launch shape of the timed step")
@@ -222,6 +222,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------- multi-rank --
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (every rank gets it); the identity with one rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time.
+    Ranks are replicas (each decomposes its own copy of the workload), so the units add up."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ------------------------------------------------------------------------------- our arm --
 def event_time(fn, steps, stream):
     import torch
@@ -297,11 +316,8 @@ def run_ours(args):
         t_end = time.time()
         barrier()
     clocks = sampler.summary(t_start, t_end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ncoef / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, dev)
+    value = aggregate_rate(ncoef, world, ms)
 
     # accuracy on sampled coefficients (oracle) -- rank 0
     res = {}
@@ -335,10 +351,7 @@ def run_ours(args):
     eb.record(stream)
     eb.synchronize()
     e2e_ms = ea.elapsed_time(eb) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     del G_pin, out_pins, G_devs, out_devs
 
     if rank != 0:
@@ -363,7 +376,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": workload_config(N, world),
             "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": world * ncoef / (e2e_ms * 1e-3), "unit": "coeffs/s",
+            "e2e": {"value": aggregate_rate(ncoef, world, e2e_ms), "unit": "coeffs/s",
                     "h2d_bytes_per_step": ncoef * es, "d2h_bytes_per_step": ncoef * es, "ms_per_step": e2e_ms,
                     "steps": e2e_steps,
                     "mode": "pauli_decompose_host_stream over the steps from pinned buffers: copy-in, decomposition and copy-out of consecutive steps pipelined over two device buffer sets"},
