@@ -489,6 +489,19 @@ def n12_forms(pg, workloads, dev, oracle, timed, forms):
                                             "hbm_gbs_algorithmic": 2 * 4 ** N * 8 / (ms * 1e-3) / 1e9,
                                             "tolerance_rel": 2e-6}
         del g, o, gs, os_
+    # a real matrix (the general input's real part): 8 B read + 8 B written per coefficient
+    Gr = np.ascontiguousarray(workloads.gaussian_complex(N, workloads.SEEDS["n12"]).real)
+    gr = torch.from_numpy(Gr).to(dev)
+    r = torch.empty(4 ** N, dtype=torch.float64, device=dev)
+    ms = timed(lambda: pg.decompose_real(gr, out=r), 20)
+    idx = workloads.sample_indices(N, workloads.SEEDS["n12_idx"])
+    want = oracle.real_coefficients_at(Gr, idx)
+    forms["n12_real_xordiag_c128"] = {
+        "ms": ms, "coeffs_per_s": 4 ** N / (ms * 1e-3),
+        "max_err_rel": float(np.max(np.abs(r.cpu().numpy()[idx.astype(np.int64)] - want)) / np.max(np.abs(Gr))),
+        "hbm_gbs_algorithmic": 4 ** N * (8 + 8) / (ms * 1e-3) / 1e9,
+        "input": "real part of the N=12 general matrix (float64)"}
+    del gr, r
 
 
 def c64_form(pg, workloads, dev, oracle, timed, forms, G14):

@@ -103,6 +103,17 @@ int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* 
 int pauli_decompose_hermitian_upper(const void* G, int N, int count, int dtype, void* out_re, int method,
                                     void* stream);
 
+/* Decomposition of real matrices. G_real: `count` row-major D x D float64 matrices (8 bytes per
+ * element; dtype must be PAULI_C128, PAULI_ERR_UNSUPPORTED otherwise). For real G every
+ * XOR-diagonal is real and so is its Walsh-Hadamard transform, so c_n is real when P_n has an
+ * even number k of Y factors and imaginary when k is odd (each Y entry is imaginary, Eq. (3)).
+ * out_re: count * 4^N float64, the real number a_n with c_n = i^(k mod 2) a_n, that is
+ * Re c_n for even k and Im c_n for odd k. Reads 8 and writes 8 bytes per coefficient instead of
+ * 16 and 16. Same kernels and launch shapes as pauli_decompose (complex128 arithmetic with zero
+ * imaginary parts), so a_n equals, bit for bit, the nonzero part that pauli_decompose stores for
+ * G + 0i with the same launch shape. */
+int pauli_decompose_real(const void* G_real, int N, int count, int dtype, void* out_re, int method, void* stream);
+
 /* Compose: G_out[k] = 2^scale_exp * sum_n c[k * 4^N + n] P_n                         Eq. (1).
  * scale_exp in [-64, 64] is an exact power-of-two factor; scale_exp = -N gives the adjoint
  * of pauli_decompose (the gradient of a real loss with respect to G is

@@ -166,3 +166,24 @@ def weighted_norm_grad(c: np.ndarray, w: np.ndarray, g: float = 1.0) -> np.ndarr
     if c.shape[-1] != w.size:
         raise ValueError("w must hold one weight per coefficient index")
     return (2.0 * g * w) * c
+
+
+def y_count(idx, N: int) -> np.ndarray:
+    """Number of Y factors of P_n for each n: base-4 digits of n equal to 2 (Eq. (2): digit t of n
+    names operator t as I, X, Y, Z for 0..3)."""
+    n = np.asarray(idx, dtype=np.uint64).ravel()
+    k = np.zeros(n.shape, dtype=np.int64)
+    for t in range(N):
+        k += ((n >> np.uint64(2 * t)) & np.uint64(3)) == 2
+    return k
+
+
+def real_coefficients_at(G_real: np.ndarray, idx) -> np.ndarray:
+    """For a real matrix G: the real a_n with c_n = i^(k mod 2) a_n, k = y_count(n) (c_n is real
+    for even k and imaginary for odd k, since every Y entry is imaginary, Eq. (3)). Computed as
+    c_n (decompose_at of G + 0i) times (-i)^(k mod 2); the discarded part is exactly zero."""
+    G = np.asarray(G_real, dtype=np.float64)
+    N = _nqubits(G)
+    c = decompose_at(G.astype(np.complex128), idx)
+    k = y_count(idx, N)
+    return np.where(k % 2 == 1, (c * -1j).real, c.real)

@@ -8,8 +8,9 @@ inputs and imports nothing else from the package.
 from .api import (PauliDecompose, PauliDecomposeWeightedNorm, PauliError, PauliPlan,  # noqa: F401
                   PauliWeightedNorm, coeffs_at, compose, compose_weighted, debug_fail_next_launches,
                   debug_stall_next_tiled, decompose, decompose_autograd, decompose_hermitian, decompose_host,
-                  decompose_host_stream, decompose_list, decompose_weighted_norm, decompose_weighted_norm_autograd,
-                  get_variant, last_error, pauli_coeffs_at, pauli_compose, pauli_compose_weighted, pauli_decompose,
-                  pauli_decompose_hermitian, pauli_decompose_host, pauli_decompose_host_stream, pauli_decompose_list,
+                  decompose_host_stream, decompose_list, decompose_real, decompose_weighted_norm,
+                  decompose_weighted_norm_autograd, get_variant, last_error, pauli_coeffs_at, pauli_compose,
+                  pauli_compose_weighted, pauli_decompose, pauli_decompose_hermitian, pauli_decompose_host,
+                  pauli_decompose_host_stream, pauli_decompose_list, pauli_decompose_real,
                   pauli_decompose_weighted_norm, pauli_weighted_norm, pauli_weighted_norm_grad, set_variant,
                   stream_status, version, weighted_norm, weighted_norm_autograd, weighted_norm_grad)

@@ -26,6 +26,7 @@ SIGNATURES = {
     "pauli_decompose": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_compose": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_decompose_hermitian": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
+    "pauli_decompose_real": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_decompose_hermitian_upper": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_weighted_norm": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
     "pauli_decompose_weighted_norm": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp]),

@@ -96,6 +96,23 @@ def pauli_decompose_hermitian(G: torch.Tensor, out: torch.Tensor | None = None, 
     return out
 
 
+def pauli_decompose_real(G: torch.Tensor, out: torch.Tensor | None = None, method="auto", stream=None) -> torch.Tensor:
+    """For a real float64 (..., 2^N, 2^N) CUDA tensor: the real a_n with c_n = i^(k mod 2) a_n
+    (k = number of Y factors of P_n), a float64 (..., 4^N) tensor."""
+    _device_tensor(G, "G")
+    if G.dtype != torch.float64:
+        raise TypeError("G must be float64")
+    N = _qubits_of_matrix(G)
+    if out is None:
+        out = torch.empty(G.shape[:-2] + (4 ** N,), dtype=torch.float64, device=G.device)
+    _device_tensor(out, "out")
+    if out.dtype != torch.float64 or out.numel() != G.numel():
+        raise ValueError("out must hold one float64 per coefficient")
+    check(_lib.load().pauli_decompose_real(G.data_ptr(), N, G.numel() // 4 ** N, PAULI_C128, out.data_ptr(),
+                                           _method(method), _stream(stream)))
+    return out
+
+
 def pauli_compose(c: torch.Tensor, out: torch.Tensor | None = None, scale_exp: int = 0, stream=None) -> torch.Tensor:
     """G = 2^scale_exp sum_n c_n P_n for a (..., 4^N) complex CUDA tensor; returns (..., 2^N, 2^N)."""
     _device_tensor(c, "c")
@@ -458,6 +475,7 @@ decompose_list = pauli_decompose_list
 decompose_host = pauli_decompose_host
 decompose_host_stream = pauli_decompose_host_stream
 decompose_hermitian = pauli_decompose_hermitian
+decompose_real = pauli_decompose_real
 weighted_norm = pauli_weighted_norm
 decompose_weighted_norm = pauli_decompose_weighted_norm
 compose_weighted = pauli_compose_weighted

@@ -220,6 +220,29 @@ int pauli_decompose_hermitian_upper(const void* G, int N, int count, int dtype, 
   return PAULI_OK;
 }
 
+int pauli_decompose_real(const void* G_real, int N, int count, int dtype, void* out_re, int method, void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if (dtype != PAULI_C128) return fail(PAULI_ERR_UNSUPPORTED, "pauli_decompose_real takes float64 matrices (PAULI_C128)");
+  if ((st = check_n(N))) return st;
+  if (count < 1) return fail(PAULI_ERR_ARG, "count = %d must be >= 1", count);
+  if (!G_real) return fail(PAULI_ERR_NULL, "G_real is NULL");
+  if (!out_re) return fail(PAULI_ERR_NULL, "out_re is NULL");
+  if ((st = check_aligned(G_real, 8, "G_real"))) return st;
+  if ((st = check_aligned(out_re, 8, "out_re"))) return st;
+  const unsigned long long per = 1ull << (2 * N);
+  if ((unsigned long long)count > (~0ull / 8) / per) return fail(PAULI_ERR_ARG, "count * 4^N overflows");
+  const size_t bytes = (size_t)(per * (unsigned long long)count) * 8;
+  if (overlaps(G_real, bytes, out_re, bytes)) return fail(PAULI_ERR_ALIAS, "G_real and out_re overlap");
+  int m = 0;
+  if ((st = resolve_method(method, N, &m))) return st;
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e = m == PAULI_XORDIAG ? pauli::launch_xordiag_real(G_real, N, count, out_re, (cudaStream_t)stream)
+                                     : pauli::launch_plain_decompose_real(G_real, N, count, out_re, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_real launch");
+  return PAULI_OK;
+}
+
 int pauli_compose(const void* c, int N, int count, int dtype, void* G_out, int scale_exp, void* stream) {
   int st = check_pair(c, "c", N, count, dtype, G_out, "G_out");
   if (st) return st;

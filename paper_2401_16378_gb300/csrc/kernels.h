@@ -10,6 +10,10 @@ namespace pauli {
 // upper triangle.
 cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s,
                                    bool re = false, bool upper = false);
+// Real (float64) G: count * 4^N reals a_n with c_n = i^(k mod 2) a_n, k the number of Y factors
+// of P_n (xordiag_real.cu, tiled_real_r4.cu).
+cudaError_t launch_xordiag_real(const void* G, int N, long long count, void* out, cudaStream_t s);
+cudaError_t launch_plain_decompose_real(const void* G, int N, long long count, void* out, cudaStream_t s);
 // Hermitian G read from its upper triangle, real coefficients, N = 7..12 (xordiag_herm_*.cu).
 cudaError_t launch_xordiag_herm_upper(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s);
 // w, g (nullable): compose g w_n c_n instead of c_n.

@@ -69,7 +69,9 @@ struct AccC64 {
 // RE: store only Re c_n, into an array of reals (Hermitian decomposition). UPPER (with RE): G is
 // Hermitian and read from its upper triangle; an element below the diagonal, G[r, r ^ x] with
 // bit h of r set (h the top set bit of x), is read as conj(G[r ^ x, r]).
-template <bool C64, bool RE, bool UPPER = false>
+// REALIN (complex128 arithmetic, with RE): G is a real float64 matrix; the output is the real
+// a_n with c_n = i^(k mod 2) a_n, k = popc(x & z) the number of Y factors.
+template <bool C64, bool RE, bool UPPER = false, bool REALIN = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(const void* __restrict__ Gv, int N,
                                                                              long long count, void* __restrict__ outv) {
   using Acc = typename std::conditional<C64, AccC64, AccC128>::type;
@@ -135,7 +137,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
         }
         const uint32_t r = rsub | ((g ^ (g >> 1)) << lrs);
         double2 e;
-        if (UPPER && hx < 32u && ((r >> hx) & 1u)) {
+        if (REALIN) {
+          e = make_double2(__ldg(&reinterpret_cast<const double*>(Gv)[kmat * (unsigned long long)D * D +
+                                                                       (unsigned long long)r * D + (r ^ x)]),
+                           0.0);
+        } else if (UPPER && hx < 32u && ((r >> hx) & 1u)) {
           e = __ldg(&G[(unsigned long long)(r ^ x) * D + r]);
           e.y = -e.y;
         } else {
@@ -172,7 +178,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
     double re = tr[k] * scale, im = ti[k] * scale;
     mul_i_pow(re, im, (uint32_t)__popc(x & z));
     const unsigned long long n = kmat * nco + pauli_index(x, z);
-    if (RE) {
+    if (REALIN) {
+      reinterpret_cast<double*>(outv)[n] = (__popc(x & z) & 1) ? im : re;
+    } else if (RE) {
       if (C64)
         reinterpret_cast<float*>(outv)[n] = (float)re;
       else
@@ -318,6 +326,15 @@ cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c
                   : (re ? (upper ? plain_decompose_kernel<false, true, true> : plain_decompose_kernel<false, true>)
                         : plain_decompose_kernel<false, false>);
   kern<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_decompose_real(const void* G, int N, long long count, void* out, cudaStream_t s) {
+  const int lcw = N < 3 ? N : 3, lkz = lcw;
+  const unsigned long long tiles = ((1ull << N) >> lcw) * ((1ull << N) >> lkz) * (unsigned long long)count;
+  const unsigned long long blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
+  plain_decompose_kernel<false, true, false, true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
   return cudaGetLastError();
 }
 

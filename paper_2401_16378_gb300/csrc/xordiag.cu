@@ -42,6 +42,8 @@ cudaError_t xordiag_c64_compose(int, int, const void*, long long, int, void*, cu
 cudaError_t xordiag_re_decompose_c128(int, const void*, long long, void*, cudaStream_t, bool);
 cudaError_t xordiag_re_decompose_c64(int, const void*, long long, void*, cudaStream_t, bool);
 cudaError_t xordiag_herm_upper_c128(int, const void*, long long, void*, cudaStream_t);
+cudaError_t xordiag_real_decompose(int, const void*, long long, void*, cudaStream_t, bool);
+cudaError_t tiled_launch_real_r4(const void*, int, int, void*, cudaStream_t);
 cudaError_t xordiag_herm_upper_c64(int, const void*, long long, void*, cudaStream_t);
 
 namespace {
@@ -124,6 +126,18 @@ cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, 
   const bool unit4096 = (v == kVariantUnit12 || v == kVariantUnit12x8) && N <= 14;
   return c64 ? xordiag_re_decompose_c64(N, in, count, out, s, unit4096)
              : xordiag_re_decompose_c128(N, in, count, out, s, unit4096);
+}
+
+// Real (float64) input: the tiled kernel where the complex128 decomposition's chosen shape is
+// tiled (16 elements per thread), else single-pass units of the chosen size.
+cudaError_t launch_xordiag_real(const void* in, int N, long long count, void* out, cudaStream_t s) {
+  if (!xordiag_supported(N)) return cudaErrorNotSupported;
+  const int v = xordiag_get_variant(N, false, false, count > 1);
+  if ((v == kVariantTiled8 || v == kVariantTiled16) && tiled_supported(N) && count <= kTiledMaxCount &&
+      !(reinterpret_cast<uintptr_t>(in) & 15u))
+    return tiled_launch_real_r4(in, N, (int)count, out, s);
+  const bool unit4096 = (v == kVariantUnit12 || v == kVariantUnit12x8) && N <= 14;
+  return xordiag_real_decompose(N, in, count, out, s, unit4096);
 }
 
 cudaError_t launch_xordiag_herm_upper(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s) {

@@ -105,6 +105,10 @@ def test_hermitian_and_norm_reject_bad_arguments(lib):
     assert lib.pauli_decompose_hermitian_upper(P(1 << 32), 13, 1, C128, P(2 << 32), 0, None) == UNSUP
     assert lib.pauli_decompose_hermitian_upper(P(A), 4, 1, C128, P(A + 8), 0, None) == ALIAS
     assert lib.pauli_decompose_hermitian_upper(P(A), 4, 1, C128, P(B), 7, None) == ARG
+    assert lib.pauli_decompose_real(P(A), 4, 1, C64, P(B), 0, None) == UNSUP
+    assert lib.pauli_decompose_real(P(A + 4), 4, 1, C128, P(B), 0, None) == ALIGN
+    assert lib.pauli_decompose_real(P(A), 4, 1, C128, P(A + 8 * 255), 0, None) == ALIAS
+    assert lib.pauli_decompose_real(P(A), 3, 1, C128, P(B), 2, None) == UNSUP
     assert lib.pauli_weighted_norm(P(A), 4, 1, C128, None, P(B), None) == NULL
     assert lib.pauli_weighted_norm(P(A), 4, 1, C128, P(B), P(A + 8), None) == ALIAS  # loss inside c
     assert lib.pauli_weighted_norm(P(A), 4, 1, C128, P(B + 4), P(B + 4096), None) == ALIGN

@@ -284,6 +284,27 @@ def test_real_part_is_the_hermitian_part(N):
     assert np.max(np.abs(oracle.decompose_full(H).imag)) <= 1e-14
 
 
+def test_real_matrix_coefficients():
+    """Real G: c_n is real for an even number of Y factors and imaginary for an odd number (each
+    Y entry is imaginary, Eq. (3)), exactly in the oracle's sums; iY (real) decomposes to the
+    one-hot a_Y = 1, and X (x) iY to the one-hot a at the (X, Y) index."""
+    iY = np.array([[0.0, 1.0], [-1.0, 0.0]])
+    a = oracle.real_coefficients_at(iY, range(4))
+    np.testing.assert_array_equal(a, [0.0, 0.0, 1.0, 0.0])
+    X = np.array([[0.0, 1.0], [1.0, 0.0]])
+    a2 = oracle.real_coefficients_at(np.kron(X, iY), range(16))
+    want = np.zeros(16)
+    want[4 * 1 + 2] = 1.0  # operator 1 = X (digit 1), operator 0 = Y (digit 2)
+    np.testing.assert_array_equal(a2, want)
+    N = 3
+    G = np.random.default_rng(350).normal(size=(8, 8))
+    c = oracle.decompose_full(G.astype(np.complex128))
+    k = oracle.y_count(range(4 ** N), N)
+    assert np.all(c.imag[k % 2 == 0] == 0.0) and np.all(c.real[k % 2 == 1] == 0.0)
+    a = oracle.real_coefficients_at(G, range(4 ** N))
+    np.testing.assert_array_equal(np.where(k % 2 == 1, c.imag, c.real), a)
+
+
 def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.decompose_at(np.zeros((3, 3)), [0])
