@@ -56,7 +56,7 @@ typedef enum {
   PAULI_ERR_DTYPE = 5,    /* dtype is not PAULI_C64 or PAULI_C128                        */
   PAULI_ERR_NOMEM = 6,    /* a plan could not allocate its device memory                 */
   PAULI_ERR_CUDA = 7,     /* a CUDA call failed (launch, copy, device query)             */
-  PAULI_ERR_TIMEOUT = 8,  /* a bounded device-side wait gave up (plans only)             */
+  PAULI_ERR_TIMEOUT = 8,  /* a bounded device-side wait gave up (plans, tiled kernel)    */
   PAULI_ERR_UNSUPPORTED = 9 /* valid request this build does not implement (e.g. method) */
 } pauli_status;
 
