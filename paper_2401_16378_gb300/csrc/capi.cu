@@ -150,11 +150,21 @@ cudaError_t host_pipe(HostPipe** out) {
     }
   HostPipe* hp = new (std::nothrow) HostPipe;
   if (!hp) return cudaErrorMemoryAllocation;
-  for (cudaStream_t* s : {&hp->in, &hp->comp, &hp->out})
-    if ((e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking)) != cudaSuccess) return e;
-  for (cudaEvent_t* ev : {&hp->start, &hp->end, &hp->in_done[0], &hp->in_done[1], &hp->comp_done[0],
-                          &hp->comp_done[1], &hp->out_done[0], &hp->out_done[1]})
-    if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  cudaStream_t* streams[] = {&hp->in, &hp->comp, &hp->out};
+  cudaEvent_t* events[] = {&hp->start, &hp->end, &hp->in_done[0], &hp->in_done[1], &hp->comp_done[0],
+                           &hp->comp_done[1], &hp->out_done[0], &hp->out_done[1]};
+  for (cudaStream_t* s : streams)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : events)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {  // release what was created
+    for (cudaEvent_t* ev : events)
+      if (*ev) cudaEventDestroy(*ev);
+    for (cudaStream_t* s : streams)
+      if (*s) cudaStreamDestroy(*s);
+    delete hp;
+    return e;
+  }
   g_pipes.emplace_back(dev, hp);
   *out = hp;
   return cudaSuccess;
