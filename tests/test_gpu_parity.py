@@ -360,3 +360,21 @@ def test_host_stream_pipeline_matches_per_matrix(dtype):
     torch.cuda.synchronize()
     for G, o in zip(mats, outs):
         np.testing.assert_array_equal(o.numpy(), host(pg.decompose(dev(G))))
+
+
+@pytest.mark.parametrize("N", [5, 8, 12, 13])
+def test_transpose_flips_sign_of_odd_y_strings(N):
+    """c_n(G^T) = (-1)^(number of Y factors) c_n(G): G^T has the same XOR-diagonals, each
+    reversed by r -> r ^ x, which multiplies the transform by (-1)^popc(x & z). The fixed-point
+    transform is exact, so the single-pass kernels agree bit for bit; the plain FP64 sum (N = 5)
+    adds the same terms in another order, and the tiled kernel (N = 13) re-scales per tile, whose
+    contents differ between G and G^T, so these agree to rounding."""
+    G = workloads.gaussian_complex(N, 870 + N)
+    a = host(pg.decompose(dev(G)))
+    b = host(pg.decompose(dev(np.ascontiguousarray(G.T))))
+    k = oracle.y_count(np.arange(4 ** N), N)
+    want = np.where(k % 2 == 1, -1.0, 1.0) * a
+    if 6 <= N <= 12:
+        np.testing.assert_array_equal(b, want)
+    else:
+        assert np.max(np.abs(b - want)) <= 2 * TOL[torch.complex128] * maxabs(G)
