@@ -521,6 +521,19 @@ def c64_form(pg, workloads, dev, oracle, timed, forms, G14):
                                 "max_err_rel": float(np.max(np.abs(got - want)) / np.max(np.abs(G64))),
                                 "tolerance_rel": 2e-6}
     del g, o, G64
+    # listed coefficients (pauli_coeffs_at, O(2^N) each, no scratch): the 4096 sampled indices
+    # of the N=14 complex128 matrix
+    g = torch.from_numpy(G14).to(dev)
+    idx_d = torch.from_numpy(idx.astype(np.int64)).to(dev)
+    oc = torch.empty(idx.size, dtype=torch.complex128, device=dev)
+    ms = timed(lambda: pg.coeffs_at(g, idx_d, out=oc), 10)
+    want = oracle.decompose_at(G14, idx)
+    forms["n14_coeffs_at_c128"] = {
+        "ms": ms, "coeffs": int(idx.size), "coeffs_per_s": idx.size / (ms * 1e-3),
+        "gbs_read": idx.size * (1 << N) * 16 / (ms * 1e-3) / 1e9,
+        "max_err_rel": float(np.max(np.abs(oc.cpu().numpy() - want)) / np.max(np.abs(G14))),
+        "note": "each coefficient reads one XOR-diagonal of G (2^N elements, 16 B each) in the paper's per-coefficient form"}
+    del g, idx_d, oc
 
 
 def batched_forms(pg, workloads, dev, oracle, timed, forms):
