@@ -1,6 +1,8 @@
 // xordiag_kernels.cuh -- kernels, launchers and per-shape dispatch of the XOR-diagonal path
 // (included by the per-dtype translation units xordiag_*.cu).
 #pragma once
+#include <type_traits>
+
 #include "kernels.h"
 #include "xordiag_impl.cuh"
 
@@ -29,8 +31,14 @@ __global__ void __launch_bounds__(Unit<UB, RB>::kThreads, Unit<UB, RB>::kMinBloc
   const unsigned long long units_per_mat = D >> K;
   const unsigned long long unit = blockIdx.x;
   const unsigned long long nu = unit + ahead;
+  // The L2 prefetch of the next wave's unit pays where a unit's row segments are short and the
+  // CTAs few; measured on GB300 it costs time (issue slots and load-queue entries) for
+  // 4096-element units from N = 10 on, for 8192-element decompositions at N = 12 and for
+  // complex64 8192-element compositions at N = 12.
+  constexpr bool kPrefetch =
+      UB == 13 ? (N <= 11 || (COMPOSE && !std::is_same<AR, ArC64>::value)) : N <= 9;
   auto prefetch_ahead = [&]() {
-    if (nu < units)
+    if (kPrefetch && nu < units)
       unit_prefetch<UB, RB, N, AR, COMPOSE>(in, (nu / units_per_mat) * (unsigned long long)D * D,
                                             (uint32_t)(nu % units_per_mat) << K, t);
   };
