@@ -9,17 +9,18 @@
 // writes the 4^N coefficients once. Composition (Eq. (1)) is the inverse map:
 //   G[r, r ^ x] = sum_z (-1)^popc(r&z) (-i)^popc(x&z) c(x, z).
 //
-// Work unit: 8192 elements, 16 per thread of a 512-thread CTA, held in registers. For
-// N <= 12 a unit is 2^K consecutive XY-masks (the "classes", K = 13 - N) times all 2^N rows,
-// in one CTA. Consecutive x share DRAM sectors (G[r, r^x] and G[r, r^x^1] are adjacent),
-// and their coefficients n(x, z), n(x^1, z) are adjacent too, so a unit reads and writes
-// whole sectors. For N >= 13 a unit is one class pair (x, x^1) over all rows, shared by a
-// cluster of 2^(N-12) CTAs (see xordiag_cluster_kernel).
+// Work unit (single-pass kernels): 8192 elements, 16 per thread of a 512-thread CTA (or 4096
+// on 256 threads, or 8 per thread on twice the threads), held in registers. For N <= 12 a
+// unit is 2^K consecutive XY-masks (the "classes", K = 13 - N) times all 2^N rows, in one CTA.
+// Consecutive x share DRAM sectors (G[r, r^x] and G[r, r^x^1] are adjacent), and their
+// coefficients n(x, z), n(x^1, z) are adjacent too, so a unit reads and writes whole sectors.
+// For N >= 13 a unit is one class pair (x, x^1) over all rows, shared by a cluster of
+// 2^(N-12) CTAs (see xordiag_cluster_kernel).
 // The transform runs in register phases of up to 4 butterfly stages, with the data
 // re-distributed between threads through shared memory (XOR-swizzled 16-byte slots).
-// The kernels are persistent: each CTA (or cluster) walks a strided list of units and,
-// while it computes one, prefetches the rows of its next unit into L2, so HBM stays busy
-// during the arithmetic and the stores of one unit drain while the next one computes.
+// One unit per CTA (cluster), in blockIdx order; where it pays, each CTA prefetches into L2
+// the rows of the unit one resident wave ahead, so HBM stays busy during the arithmetic.
+// Decompositions at N = 13, 14 default to the two-stage tiled kernel (tiled_impl.cuh).
 //
 // Arithmetic:
 //  complex128: every class is converted to int64 fixed point with a per-class power-of-two
