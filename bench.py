@@ -379,7 +379,8 @@ def run_ours(args):
             "e2e": {"value": aggregate_rate(ncoef, world, e2e_ms), "unit": "coeffs/s",
                     "h2d_bytes_per_step": ncoef * es, "d2h_bytes_per_step": ncoef * es, "ms_per_step": e2e_ms,
                     "steps": e2e_steps,
-                    "mode": "pauli_decompose_host_stream over the steps from pinned buffers: copy-in, decomposition and copy-out of consecutive steps pipelined over two device buffer sets"},
+                    "mode": ("pauli_decompose_host_stream over the steps from pinned buffers: copy-in, decomposition "
+                             "and copy-out of consecutive steps pipelined over two device buffer sets")},
             "gpu_launches": args.steps, "clocks": clocks, "accuracy": res}
     if not args.quick:
         line["forms"] = secondary_forms(pg, workloads, dev, stream, G_h)
