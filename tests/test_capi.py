@@ -163,3 +163,19 @@ def test_injected_launch_failure_is_reported(lib):
     assert lib.pauli_decompose(P(A), 4, 1, C128, P(B), 0, None) == CUDA
     assert b"injected" in lib.pauli_last_error()
     lib.pauli_debug_fail_next_launches(0)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/pauli.h compiles as C99 (no C++ or torch types at the boundary)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "pauli.h"\nint main(void) { return pauli_version() < 0; }\n')
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                          "-I", os.path.join(root, "include"), str(src)], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
