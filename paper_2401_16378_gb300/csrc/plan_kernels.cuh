@@ -8,6 +8,8 @@
 // prefetch that item's rows into L2 while computing the current one. The counter and a
 // status word live in a small control block that the plan resets before each launch.
 #pragma once
+#include <type_traits>
+
 #include "kernels.h"
 #include "plan_internal.h"
 #include "xordiag_impl.cuh"
@@ -157,6 +159,10 @@ template <int UB, class AR, bool HERM = false>
 __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlocks))
     plan_kernel(const PlanItem* __restrict__ items, int n_items, const PlanMat* __restrict__ mats, PlanCtrl* ctrl,
                 int batch) {
+  // The next item's rows are prefetched into L2 while this one computes; measured on GB300 the
+  // prefetch pays for complex128 (general batch: 0.80 against 0.97 ms without) but not for
+  // complex64 (0.79 against 0.78 ms; Hermitian batch 0.47 against 0.44 ms).
+  constexpr bool kPrefetch = !std::is_same<AR, ArC64>::value && !std::is_same<AR, ReOut<ArC64>>::value;
   extern __shared__ __align__(16) uint4 xbuf[];
   __shared__ uint32_t smax[128];
   __shared__ int s_next;
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__((Unit<UB, 4>::kThreads), (Unit<UB, 4>::kMinBlo
     const PlanItem it = items ? items[cur] : item_from_table(cur, mats, batch);
     const PlanMat m = mats[it.mat];
     auto pf = [&]() {
-      if (nxt < n_items) {
+      if (kPrefetch && nxt < n_items) {
         const PlanItem in2 = items ? items[nxt] : item_from_table(nxt, mats, batch);
         prefetch_item(in2, mats[in2.mat], UB, esz, t, T, HERM);
       }
