@@ -153,6 +153,9 @@ def test_list_and_plan_argument_errors(lib):
     assert lib.pauli_plan_create(ns, 2, C128, 0, 0, ctypes.byref(h)) == ARG
     assert lib.pauli_plan_create(ns, 0, C128, 0, 0, ctypes.byref(h)) == ARG
     assert lib.pauli_plan_create(None, 2, C128, 0, 0, ctypes.byref(h)) == NULL
+    assert lib.pauli_plan_create_hermitian(ns, 2, C128, 0, 0, ctypes.byref(h)) == ARG  # N = 11 > 10
+    assert lib.pauli_plan_create_hermitian(ns, 2, C128, 384, 0, ctypes.byref(h)) == ARG
+    assert lib.pauli_plan_create_hermitian(ns, 2, 7, 0, 0, ctypes.byref(h)) == DTYPE
     assert lib.pauli_plan_execute(None, None) == NULL
     assert lib.pauli_decompose_list(None, ns, 2, C128, None, 0, None) == NULL
     assert lib.pauli_decompose_list(None, None, 0, C128, None, 0, None) == OK
