@@ -182,3 +182,21 @@ def test_header_is_plain_c(tmp_path):
     res = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                           "-I", os.path.join(root, "include"), str(src)], capture_output=True, text=True)
     assert res.returncode == 0, res.stderr
+
+
+def test_autotune_cache_entries_reach_the_variant_tables(lib):
+    """autotune.apply sets the one-matrix and the batch launch shapes separately (host only)."""
+    from paper_2401_16378_gb300 import autotune
+
+    cache = {"variants": {"10/c128/decompose": {"best": 4}, "10/c128/decompose_batched": {"best": 3},
+                          "10/c64/compose_batched": {"best": 1}}}
+    try:
+        assert autotune.apply(cache) == 3
+        assert lib.pauli_get_variant(10, C128, 0) == 4
+        assert lib.pauli_get_variant(10, C128, 2) == 3
+        assert lib.pauli_get_variant(10, 0, 3) == 1
+    finally:
+        for op in range(4):
+            lib.pauli_set_variant(10, C128, op, 0)
+            lib.pauli_set_variant(10, 0, op, 0)
+    assert lib.pauli_get_variant(10, C128, 2) == 2  # built-in batch shape: 4096-element units
