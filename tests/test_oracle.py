@@ -312,3 +312,75 @@ def test_rejects_bad_arguments():
         oracle.decompose_at(np.zeros((4, 4)), [16])
     with pytest.raises(ValueError):
         oracle.compose_at(np.zeros(15), [0], [0])
+
+
+# ---- the compensated sum ---------------------------------------------------------------------
+# A plain FP64 running sum of 2^N terms can lose every small term next to a large one; the
+# oracle's Neumaier sum must not. These pins use integer data whose exact sums Python integers
+# (and numpy int64) compute without rounding: a diagonal holding +-2^60 first and last and small
+# integers in between. Every partial sum of a plain running sum is then +-2^60 (the small terms
+# fall below its 256-wide ulp) and the final result loses all of them, while the compensated sum
+# returns the exactly rounded total. The diagonal matrix needs only the x = 0 coefficients
+# (Z/I strings), which are a Sylvester-Hadamard transform of the diagonal (scipy.linalg.hadamard)
+# divided by 2^N (Eq. (4) with P_n diagonal).
+
+_BIG = 2 ** 60
+
+
+def _cancelling_diagonal(N, seed):
+    """Integer diagonal: +2^60 first, -2^60 last, small integers in [-5, 5] in between."""
+    D = 1 << N
+    rng = np.random.default_rng(seed)
+    d = rng.integers(-5, 6, size=D).astype(np.int64)
+    d[0], d[-1] = _BIG, -_BIG
+    return d
+
+
+def _z_string_index(z, N):
+    """Tensor index of the string with Z where z has a set bit and I elsewhere (digit 3 = Z)."""
+    return sum(3 << (2 * t) for t in range(N) if (z >> t) & 1)
+
+
+def _exact_hadamard_over_d(d, N):
+    """round-to-nearest(H d) * 2^-N with H d in exact int64 arithmetic (|H d| < 2^62)."""
+    H = scipy.linalg.hadamard(1 << N, dtype=np.int64)
+    s = H @ d
+    return np.array([float(int(v)) for v in s]) * 2.0 ** -N  # int -> float rounds correctly
+
+
+@pytest.mark.parametrize("N", [10, 12])
+def test_compensated_sum_is_exact_on_cancelling_diagonal(N):
+    """Eq. (13) summed with compensation: bit-exact on sums that a plain FP64 sum gets wrong."""
+    D = 1 << N
+    dre = _cancelling_diagonal(N, 31 + N)
+    dim = _cancelling_diagonal(N, 57 + N)
+    dim[0], dim[-1] = -_BIG, _BIG  # the opposite order of signs in the imaginary part
+    G = np.zeros((D, D), dtype=np.complex128)
+    G[np.arange(D), np.arange(D)] = dre.astype(np.float64) + 1j * dim.astype(np.float64)
+    idx = np.array([_z_string_index(z, N) for z in range(D)], dtype=np.uint64)
+    got = oracle.decompose_at(G, idx)
+    np.testing.assert_array_equal(got.real, _exact_hadamard_over_d(dre, N))
+    np.testing.assert_array_equal(got.imag, _exact_hadamard_over_d(dim, N))
+    # the identity coefficient is the trace / 2^N: the small terms alone survive the cancellation
+    assert got[0].real == float(int(dre[1:-1].sum())) * 2.0 ** -N
+    assert got[0].real != 0.0  # what a plain running sum returns
+
+
+def test_compensated_sum_is_exact_in_composition():
+    """Eq. (1) summed with compensation: [G]_{rr} = sum over I/Z strings n of c_n (-1)^popc(r & z(n)),
+    i.e. the Sylvester-Hadamard transform of the I/Z coefficients, exact in int64 and rounded once."""
+    N = 8
+    D = 1 << N
+    cz = _cancelling_diagonal(N, 91)  # c of the I/Z string with Z-mask z, for z = 0 .. D-1
+    c = np.zeros(4 ** N, dtype=np.complex128)
+    for z in range(D):
+        c[_z_string_index(z, N)] = float(cz[z])
+    # n = 0 (all I) holds +2^60 and n = 4^N - 1 (all Z) holds -2^60: first and last in the sum
+    assert c[0] == _BIG and c[4 ** N - 1] == -_BIG
+    r = np.arange(D, dtype=np.uint64)
+    got = oracle.compose_at(c, r, r)
+    H = scipy.linalg.hadamard(D, dtype=np.int64)
+    want = np.array([float(int(v)) for v in H @ cz])
+    np.testing.assert_array_equal(got.real, want)
+    assert np.all(got.imag == 0)
+    assert got[0].real == float(int(cz[1:-1].sum())) and got[0].real != 0.0

@@ -7,6 +7,7 @@ import subprocess
 
 import numpy as np
 import pytest
+import scipy.linalg
 
 from oracle import kron
 from paper_2401_16378_gb300 import workloads
@@ -23,6 +24,14 @@ MUTANTS = {
     "xy_mask_wrong": ("if (p == 1u || p == 2u)", "if (p == 1u || p == 3u)"),
     "lambda_column_wrong": ("unsigned b = a ^ bit_of(m, t);", "unsigned b = a;"),
     "imag_term_sign": ("nsum_add(&si, lr * g[1] + li * g[0]);", "nsum_add(&si, lr * g[1] - li * g[0]);"),
+    # the compensated sum: its value without the compensation, the branch for the larger
+    # running sum using the other branch's formula, a plain running sum, and the composition
+    # returning its sums without their compensation
+    "neumaier_value_drops_comp": ("return a->sum + a->comp;", "return a->sum;"),
+    "neumaier_branch_swapped": ("a->comp += (a->sum - t) + x;\n  else", "a->comp += (x - t) + a->sum;\n  else"),
+    "neumaier_plain_sum": ("double t = a->sum + x;\n", "double t = a->sum + x;\n  a->sum = t;\n  return;\n"),
+    "compose_compensation_dropped": ("out[0] = nsum_value(&sr);\n  out[1] = nsum_value(&si);",
+                                     "out[0] = sr.sum;\n  out[1] = si.sum;"),
 }
 
 
@@ -39,6 +48,8 @@ def _build(tmp_path, name, old, new):
     u64p = ctypes.POINTER(ctypes.c_uint64)
     L.oracle_decompose_at.argtypes = [dp, ctypes.c_int, u64p, ctypes.c_int64, dp, ctypes.c_int]
     L.oracle_decompose_at.restype = ctypes.c_int
+    L.oracle_compose_at.argtypes = [dp, ctypes.c_int, u64p, u64p, ctypes.c_int64, dp, ctypes.c_int]
+    L.oracle_compose_at.restype = ctypes.c_int
 
     def decompose_full(G):
         G = np.ascontiguousarray(G, dtype=np.complex128)
@@ -50,10 +61,40 @@ def _build(tmp_path, name, old, new):
         assert rc == 0
         return out
 
-    return decompose_full
+    def compose_diag(c):
+        c = np.ascontiguousarray(c, dtype=np.complex128)
+        N = (c.size.bit_length() - 1) // 2
+        r = np.arange(1 << N, dtype=np.uint64)
+        out = np.empty(r.size, dtype=np.complex128)
+        rc = L.oracle_compose_at(c.ctypes.data_as(dp), N, r.ctypes.data_as(u64p), r.ctypes.data_as(u64p), r.size,
+                                 out.ctypes.data_as(dp), 1)
+        assert rc == 0
+        return out
+
+    return decompose_full, compose_diag
 
 
-def _pins_pass(decompose_full):
+def _compensation_pins_pass(decompose_full, compose_diag):
+    """The exact cancelling-diagonal pins of test_oracle.py at N = 6 (Eqs. (13) and (1))."""
+    N, D, big = 6, 64, 2 ** 60
+    rng = np.random.default_rng(5)
+    d = rng.integers(-5, 6, size=D).astype(np.int64)
+    d[0], d[-1] = big, -big
+    H = scipy.linalg.hadamard(D, dtype=np.int64)
+    exact = np.array([float(int(v)) for v in H @ d])
+    zidx = np.array([sum(3 << (2 * t) for t in range(N) if (z >> t) & 1) for z in range(D)])
+    G = np.diag(d.astype(np.float64)).astype(np.complex128)
+    if not np.array_equal(decompose_full(G)[zidx].real, exact * 2.0 ** -N):
+        return False
+    c = np.zeros(4 ** N, dtype=np.complex128)
+    c[zidx] = d.astype(np.float64)
+    return np.array_equal(compose_diag(c).real, exact)
+
+
+def _pins_pass(fns):
+    decompose_full, compose_diag = fns
+    if not _compensation_pins_pass(decompose_full, compose_diag):
+        return False
     G1 = np.array([[1, 2], [3, 4]], dtype=np.complex128)
     if not np.array_equal(decompose_full(G1), np.array([2.5, 2.5, -0.5j, -1.5])):
         return False
