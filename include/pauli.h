@@ -69,10 +69,37 @@ typedef enum {
  *   out[k * 4^N + n] = c_n of matrix k = 2^-N Tr(P_n G_k)              Eq. (4), via Eq. (13).
  * dtype applies to both G and out. method: pauli_method.
  * With PAULI_XORDIAG at N = 13 and 14 the built-in launch shape is a tiled one (see
- * PAULI_VARIANT_TILED8 below), which allocates a scratch buffer (48 MiB at N = 14, 40 MiB at
- * N = 13) with cudaMalloc at its first use on each (device, stream) pair and keeps it: make
- * the first such call on a stream before capturing that stream into a CUDA graph. */
+ * PAULI_VARIANT_TILED8 below) that needs a scratch ring between its two stages. This entry point
+ * takes it from a library-owned buffer per (device, stream), allocated with cudaMalloc at the
+ * first tiled call on that pair, sized for every N so that it is never replaced, and kept until
+ * pauli_release_workspaces: make the first such call on a stream before capturing that stream
+ * into a CUDA graph. Callers that own their memory use pauli_decompose_ws instead. */
 int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int method, void* stream);
+
+/* Bytes of caller-provided scratch that pauli_decompose_ws needs for these arguments (with the
+ * launch shape currently chosen for N, dtype and count; see pauli_set_variant), written to
+ * *bytes: 0 when the call needs none, else the tiled kernel's scratch ring (tens of MiB). */
+int pauli_decompose_workspace_size(int N, int count, int dtype, int method, size_t* bytes);
+
+/* pauli_decompose with the scratch supplied by the caller: the library allocates nothing.
+ * workspace: device memory of workspace_bytes >= pauli_decompose_workspace_size(...) bytes,
+ * 256-byte aligned, not overlapping G or out (NULL allowed when the size is 0). Its contents
+ * need no initialisation; the call clears its control block on `stream` before the launch.
+ * One call at a time per workspace: calls that share a workspace must be ordered (one stream,
+ * or events). The call can be captured in a CUDA graph. pauli_workspace_status reports the
+ * call's device status. Same results, bit for bit, as pauli_decompose. */
+int pauli_decompose_ws(const void* G, int N, int count, int dtype, void* out, int method, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
+/* Synchronises `stream` and reports (then clears) the status word in a caller workspace of
+ * pauli_decompose_ws: PAULI_OK, or PAULI_ERR_TIMEOUT when a bounded wait between the tiled
+ * kernel's two stages gave up (that call's results are not valid). */
+int pauli_workspace_status(void* workspace, void* stream);
+
+/* Synchronises `stream` and frees the library-owned buffers of the current device for that
+ * stream (the tiled decomposition's scratch ring, the weighted norm's partials). Call it before
+ * destroying a stream that library calls used; a later call on the stream allocates afresh. */
+int pauli_release_workspaces(void* stream);
 
 /* Decomposition of Hermitian matrices: only the real parts are stored,
  *   out_re[k * 4^N + n] = Re c_n of matrix k                                  Eq. (4), (13).
@@ -176,6 +203,21 @@ int pauli_coeffs_at(const void* G, int N, int dtype, const uint64_t* idx, int64_
 int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch, int dtype,
                          void* const* out_list, int method, void* stream);
 
+/* Composition of a batch of coefficient vectors of uneven N in one launch (per 1024 matrices):
+ *   G_out_list[b] = 2^scale_exp * sum_n c_list[b][n] P_n          Eq. (1), for every b < batch.
+ * c_list[b]: device, 4^N_b coefficients in the order n; G_out_list[b]: device, the 2^N_b x 2^N_b
+ * matrix; the two host arrays hold device pointers, N_list is a host array of values in
+ * [1, 11]; scale_exp in [-64, 64] (scale_exp = -N_b gives the adjoint of the decomposition, when
+ * every N_b is equal). For N_b >= 6 each 4096-element XOR-diagonal unit is one work item (the
+ * transform of Eq. (1) over the Z/Y mask for 2^(12-N_b) XY-masks); smaller matrices are one
+ * item each. The matrix table is passed to the kernel by value and its CTAs take the items in a
+ * fixed order, so the call allocates nothing, keeps no state between calls, returns without
+ * waiting for the GPU and can be captured in a CUDA graph. Same arithmetic as pauli_compose
+ * (complex128: exact int64 transform of each XY-mask's values at a per-mask power-of-two scale;
+ * complex64: TwoSum-compensated FP32). Input and output buffers must not overlap. */
+int pauli_compose_batched(const void* const* c_list, const int* N_list, int batch, int dtype,
+                          void* const* G_out_list, int scale_exp, void* stream);
+
 /* Host-buffer round trip for callers whose data is in host memory: copies `count` matrices
  * from G_host (pinned memory gives asynchronous copies) to the caller's device buffer G_dev,
  * decomposes into out_dev, and copies the coefficients back to out_host, all on `stream`.
@@ -208,10 +250,13 @@ int pauli_decompose_host_stream(const void* const* G_host_list, void* const* out
  * exits). There is no counterpart in the paper; this is an interface convenience.
  *   G_list / out_list: host arrays of `batch` device pointers; N_list: host array, values in
  *   [1, 10]; 1 <= batch <= 1024 (larger batches are rejected with PAULI_ERR_ARG).
- * All calls share the array: each call resets the counter and status before its launch, and
- * calls whose kernels overlap on the GPU race on it -- serialise them (one stream, or events).
- * The first call on a device looks up the array's device address; make it before any stream
- * capture. Asynchronous like the other entry points. */
+ * The call enqueues two kernels and returns without waiting for the GPU: the first receives
+ * the matrix table by value (as a kernel parameter), writes it to the array and clears the
+ * counter and status; the second decomposes. The host arrays may be reused as soon as the call
+ * returns.
+ * All calls share the array and it keeps the last call's contents; calls whose kernels overlap
+ * on the GPU race on it -- serialise them (one stream, or events). The first call on a device
+ * looks up the array's device address; make it before any stream capture. */
 int pauli_decompose_batch_static(const void* const* G_list, const int* N_list, int batch, int dtype,
                                  void* const* out_list, void* stream);
 

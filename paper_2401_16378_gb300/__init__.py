@@ -14,3 +14,5 @@ from .api import (PauliDecompose, PauliDecomposeWeightedNorm, PauliError, PauliP
                   pauli_decompose_host_stream, pauli_decompose_list, pauli_decompose_real,
                   pauli_decompose_weighted_norm, pauli_weighted_norm, pauli_weighted_norm_grad, set_variant,
                   stream_status, version, weighted_norm, weighted_norm_autograd, weighted_norm_grad)
+from .api import (compose_batched, decompose_workspace_size, decompose_ws, pauli_decompose_workspace_size,  # noqa: F401
+                  pauli_compose_batched, pauli_decompose_ws, release_workspaces, workspace_status)

@@ -24,6 +24,10 @@ _vpp = ctypes.POINTER(ctypes.c_void_p)
 _ip = ctypes.POINTER(ctypes.c_int)
 SIGNATURES = {
     "pauli_decompose": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
+    "pauli_decompose_workspace_size": (_i, [_i, _i, _i, _i, ctypes.POINTER(ctypes.c_size_t)]),
+    "pauli_decompose_ws": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, ctypes.c_size_t, _vp]),
+    "pauli_workspace_status": (_i, [_vp, _vp]),
+    "pauli_release_workspaces": (_i, [_vp]),
     "pauli_compose": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_decompose_hermitian": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pauli_decompose_real": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
@@ -36,6 +40,7 @@ SIGNATURES = {
     "pauli_decompose_list": (_i, [_vpp, _ip, _i, _i, _vpp, _i, _vp]),
     "pauli_decompose_host": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp]),
     "pauli_decompose_host_stream": (_i, [_vpp, _vpp, _i, _i, _i, _vpp, _vpp, _i, _vp]),
+    "pauli_compose_batched": (_i, [_vpp, _ip, _i, _i, _vpp, _i, _vp]),
     "pauli_decompose_batch_static": (_i, [_vpp, _ip, _i, _i, _vpp, _vp]),
     "pauli_plan_create": (_i, [_ip, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_void_p)]),
     "pauli_plan_create_hermitian": (_i, [_ip, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_void_p)]),

@@ -75,6 +75,47 @@ def pauli_decompose(G: torch.Tensor, out: torch.Tensor | None = None, method="au
     return out
 
 
+def pauli_decompose_workspace_size(N: int, count: int = 1, dtype: torch.dtype = torch.complex128,
+                                   method="auto") -> int:
+    """Bytes of caller scratch that pauli_decompose_ws needs (0 when it needs none)."""
+    n = ctypes.c_size_t(0)
+    check(_lib.load().pauli_decompose_workspace_size(int(N), int(count), _DTYPES[dtype], _method(method),
+                                                     ctypes.byref(n)))
+    return int(n.value)
+
+
+def pauli_decompose_ws(G: torch.Tensor, workspace: torch.Tensor | None, out: torch.Tensor | None = None,
+                       method="auto", stream=None) -> torch.Tensor:
+    """pauli_decompose with caller-provided scratch (a CUDA tensor of at least
+    pauli_decompose_workspace_size bytes); the library allocates nothing."""
+    _device_tensor(G, "G")
+    N = _qubits_of_matrix(G)
+    count = G.numel() // (4 ** N)
+    if out is None:
+        out = torch.empty(G.shape[:-2] + (4 ** N,), dtype=G.dtype, device=G.device)
+    _device_tensor(out, "out")
+    if out.dtype != G.dtype or out.numel() != G.numel():
+        raise ValueError("out must match G in dtype and number of elements")
+    wp, wb = 0, 0
+    if workspace is not None:
+        _device_tensor(workspace, "workspace")
+        wp, wb = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    check(_lib.load().pauli_decompose_ws(G.data_ptr(), N, count, _dtype(G), out.data_ptr(), _method(method),
+                                         ctypes.c_void_p(wp), wb, _stream(stream)))
+    return out
+
+
+def workspace_status(workspace: torch.Tensor, stream=None) -> None:
+    """Synchronise the stream and raise PauliError if the last pauli_decompose_ws call that used
+    `workspace` timed out in a bounded device wait."""
+    check(_lib.load().pauli_workspace_status(ctypes.c_void_p(workspace.data_ptr()), _stream(stream)))
+
+
+def release_workspaces(stream=None) -> None:
+    """Free the library-owned scratch of the current device for `stream` (after synchronising it)."""
+    check(_lib.load().pauli_release_workspaces(_stream(stream)))
+
+
 def pauli_decompose_hermitian(G: torch.Tensor, out: torch.Tensor | None = None, method="auto", stream=None,
                               upper: bool = False) -> torch.Tensor:
     """Re c_n for a (..., 2^N, 2^N) complex CUDA tensor (all of c_n when G is Hermitian); returns
@@ -257,6 +298,22 @@ def pauli_decompose_list(Gs: Sequence[torch.Tensor], outs: Sequence[torch.Tensor
     op, keep2 = _ptr_array([o.data_ptr() for o in outs])
     narr = (ctypes.c_int * len(Ns))(*Ns)
     check(_lib.load().pauli_decompose_list(gp, narr, len(Gs), dt, op, _method(method), _stream(stream)))
+    return list(outs)
+
+
+def pauli_compose_batched(cs: Sequence[torch.Tensor], outs: Sequence[torch.Tensor] | None = None, scale_exp: int = 0,
+                          stream=None) -> list[torch.Tensor]:
+    """G_b = 2^scale_exp sum_n c_b[n] P_n for coefficient vectors of different N, in one launch."""
+    if not cs:
+        return []
+    dt = _dtype(cs[0])
+    Ns = [_qubits_of_coeffs(_device_tensor(c, "c")) for c in cs]
+    if outs is None:
+        outs = [torch.empty((1 << N, 1 << N), dtype=c.dtype, device=c.device) for c, N in zip(cs, Ns)]
+    cp, keep1 = _ptr_array([c.data_ptr() for c in cs])
+    op, keep2 = _ptr_array([o.data_ptr() for o in outs])
+    narr = (ctypes.c_int * len(Ns))(*Ns)
+    check(_lib.load().pauli_compose_batched(cp, narr, len(cs), dt, op, int(scale_exp), _stream(stream)))
     return list(outs)
 
 
@@ -472,6 +529,9 @@ decompose = pauli_decompose
 compose = pauli_compose
 coeffs_at = pauli_coeffs_at
 decompose_list = pauli_decompose_list
+compose_batched = pauli_compose_batched
+decompose_ws = pauli_decompose_ws
+decompose_workspace_size = pauli_decompose_workspace_size
 decompose_host = pauli_decompose_host
 decompose_host_stream = pauli_decompose_host_stream
 decompose_hermitian = pauli_decompose_hermitian

@@ -14,6 +14,7 @@
 #include "pauli.h"
 #include "plan_internal.h"
 #include "tiled.h"
+#include "workspace.h"
 
 namespace pauli {
 int static_batch_max();
@@ -170,6 +171,17 @@ cudaError_t host_pipe(HostPipe** out) {
   return cudaSuccess;
 }
 
+// Scratch bytes that pauli_decompose takes for these arguments (the tiled kernel's ring), or 0.
+int decompose_workspace_bytes(int N, long long count, int dtype, int method, size_t* bytes) {
+  int m = 0, st;
+  *bytes = 0;
+  if ((st = resolve_method(method, N, &m))) return st;
+  if (m != PAULI_XORDIAG || !pauli::tiled_supported(N) || count > 1024) return PAULI_OK;
+  const int v = pauli::xordiag_get_variant(N, dtype == PAULI_C64, false, count > 1);
+  if (v == pauli::kVariantTiled8 || v == pauli::kVariantTiled16) *bytes = pauli::tiled_workspace_bytes(N);
+  return PAULI_OK;
+}
+
 int decompose_checked(const void* G, int N, long long count, int dtype, void* out, int method, cudaStream_t s) {
   int m = 0, st;
   if ((st = resolve_method(method, N, &m))) return st;
@@ -197,6 +209,58 @@ int pauli_decompose(const void* G, int N, int count, int dtype, void* out, int m
   int st = check_pair(G, "G", N, count, dtype, out, "out");
   if (st) return st;
   return decompose_checked(G, N, count, dtype, out, method, (cudaStream_t)stream);
+}
+
+int pauli_decompose_workspace_size(int N, int count, int dtype, int method, size_t* bytes) {
+  int st;
+  if (!bytes) return fail(PAULI_ERR_NULL, "bytes is NULL");
+  *bytes = 0;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (count < 1) return fail(PAULI_ERR_ARG, "count = %d must be >= 1", count);
+  return decompose_workspace_bytes(N, count, dtype, method, bytes);
+}
+
+int pauli_decompose_ws(const void* G, int N, int count, int dtype, void* out, int method, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  int st = check_pair(G, "G", N, count, dtype, out, "out");
+  if (st) return st;
+  size_t need = 0;
+  if ((st = decompose_workspace_bytes(N, count, dtype, method, &need))) return st;
+  if (need) {
+    if (!workspace) return fail(PAULI_ERR_NULL, "workspace is NULL (%zu bytes needed)", need);
+    if ((st = check_aligned(workspace, 256, "workspace"))) return st;
+    if (workspace_bytes < need)
+      return fail(PAULI_ERR_ARG, "workspace_bytes = %zu is below the %zu bytes needed", workspace_bytes, need);
+    const size_t bytes = (size_t)(1ull << (2 * N)) * (size_t)count * elem_bytes(dtype);
+    if (overlaps(workspace, need, G, bytes) || overlaps(workspace, need, out, bytes))
+      return fail(PAULI_ERR_ALIAS, "workspace overlaps G or out");
+    // this call's status word starts clear (the launch clears the rest of the control block)
+    cudaError_t e = cudaMemsetAsync(workspace, 0, pauli::kTiledCtrlBytes, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_ws: clearing the workspace");
+  }
+  pauli::CallerWorkspace guard(pauli::kWorkspaceTiled, workspace, workspace_bytes);
+  return decompose_checked(G, N, count, dtype, out, method, (cudaStream_t)stream);
+}
+
+int pauli_workspace_status(void* workspace, void* stream) {
+  if (!workspace) return fail(PAULI_ERR_NULL, "workspace is NULL");
+  const cudaStream_t s = (cudaStream_t)stream;
+  int status = 0;
+  int* sp = reinterpret_cast<int*>(reinterpret_cast<char*>(workspace) + offsetof(pauli::TiledCtrl, status));
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, sp, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sp, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_workspace_status");
+  if (status) return fail(status, "a bounded wait in the tiled decomposition gave up");
+  return PAULI_OK;
+}
+
+int pauli_release_workspaces(void* stream) {
+  cudaError_t e = pauli::stream_workspace_release((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_release_workspaces");
+  return PAULI_OK;
 }
 
 int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* out_re, int method, void* stream) {
@@ -420,6 +484,28 @@ int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch
     int st = decompose_checked(G_list[b], N_list[b], 1, dtype, out_list[b], method, (cudaStream_t)stream);
     if (st) return st;
   }
+  return PAULI_OK;
+}
+
+int pauli_compose_batched(const void* const* c_list, const int* N_list, int batch, int dtype, void* const* G_out_list,
+                          int scale_exp, void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if (batch < 0) return fail(PAULI_ERR_ARG, "batch = %d must be >= 0", batch);
+  if (batch == 0) return PAULI_OK;
+  if (!c_list || !N_list || !G_out_list) return fail(PAULI_ERR_NULL, "c_list, N_list and G_out_list must not be NULL");
+  if (scale_exp < -64 || scale_exp > 64) return fail(PAULI_ERR_ARG, "scale_exp = %d outside [-64, 64]", scale_exp);
+  const int nmax = pauli::compose_batched_max_n();
+  for (int b = 0; b < batch; ++b) {
+    if (N_list[b] < 1 || N_list[b] > nmax)
+      return fail(PAULI_ERR_ARG, "N_list[%d] = %d outside [1, %d]", b, N_list[b], nmax);
+    st = check_pair(c_list[b], "c_list[b]", N_list[b], 1, dtype, G_out_list[b], "G_out_list[b]");
+    if (st) return fail(st, "entry %d: %s", b, g_err.c_str());
+  }
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e = pauli::launch_compose_batched(c_list, N_list, batch, dtype == PAULI_C64, G_out_list, scale_exp,
+                                                (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_compose_batched launch");
   return PAULI_OK;
 }
 

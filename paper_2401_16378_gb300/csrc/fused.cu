@@ -37,7 +37,7 @@ cudaError_t launch_decompose_norm(const void* G, int N, long long count, bool c6
     const bool u4 = use_unit4096(N, c64, false, count);
     const unsigned long long units = ((unsigned long long)count << (2 * N)) >> (u4 ? 12 : 13);
     void* ws = nullptr;
-    if ((e = stream_workspace(kWorkspaceNorm, st, units * sizeof(double), 0, &ws)) != cudaSuccess) return e;
+    if ((e = stream_workspace(kWorkspaceNorm, st, units * sizeof(double), kNormWorkspaceReserve, 0, &ws)) != cudaSuccess) return e;
     double* partial = static_cast<double*>(ws);
     e = c64 ? fused_decompose_norm_c64(N, u4, G, count, out, w, partial, st)
             : fused_decompose_norm_c128(N, u4, G, count, out, w, partial, st);

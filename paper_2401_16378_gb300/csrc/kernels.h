@@ -49,6 +49,11 @@ cudaError_t launch_decompose_norm(const void* G, int N, long long count, bool c6
                                   void* loss, int method, cudaStream_t s);
 cudaError_t launch_compose_weighted(const void* c, int N, long long count, bool c64, const void* w, const void* g,
                                     int scale_exp, void* G, cudaStream_t s);
+// Composition of a batch of coefficient vectors of uneven N (1 <= N <= compose_batched_max_n()),
+// host arrays of device pointers; one launch per 1024 matrices (compose_batched.cu).
+int compose_batched_max_n();
+cudaError_t launch_compose_batched(const void* const* c_list, const int* N_list, int batch, bool c64,
+                                   void* const* G_list, int scale_exp, cudaStream_t s);
 // Adds n partial losses (fixed order) into *loss (norm.cu).
 cudaError_t launch_norm_final(const double* partial, long long n, bool c64, void* loss, cudaStream_t s);
 

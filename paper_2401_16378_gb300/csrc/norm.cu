@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) grad_flat(const void* cv, const void
 cudaError_t launch_weighted_norm(const void* c, int N, long long count, bool c64, const void* w, void* loss,
                                  cudaStream_t st) {
   void* ws = nullptr;
-  cudaError_t e = stream_workspace(kWorkspaceNorm, st, kBlocks * sizeof(double), 0, &ws);
+  cudaError_t e = stream_workspace(kWorkspaceNorm, st, kBlocks * sizeof(double), kNormWorkspaceReserve, 0, &ws);
   if (e != cudaSuccess) return e;
   double* partial = static_cast<double*>(ws);
   const unsigned long long total = (unsigned long long)count << (2 * N);

@@ -10,12 +10,17 @@
 // kStaticMaxBatch matrices. The work items are not stored; the kernel finds the matrix of
 // item i by binary search over the table's running item counts.
 //
-// All calls share the array and it keeps the last call's contents; each call clears the
-// control block before its launch. Calls whose kernels overlap on the GPU (different streams,
-// or different threads without ordering) race on the array and must be serialised by the
-// caller. The first call on each device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current) and caches it; make that first call
-// before capturing the stream into a CUDA graph.
+// The table reaches the array through a small kernel that receives it by value, as a kernel
+// parameter (24 KiB at most, inside the 32 KiB parameter limit), and also clears the control
+// block. Kernel parameters are copied when the launch is enqueued, so the call returns without
+// waiting for the GPU, the caller's host arrays may be reused at once, and a graph that captured
+// a call replays that call's own table.
+//
+// All calls share the array and it keeps the last call's contents. Calls whose kernels overlap
+// on the GPU (different streams, or different threads without ordering) race on the array and
+// must be serialised by the caller. The first call on each device looks up the array's device
+// address with cudaGetSymbolAddress (with that device current) and caches it; make that first
+// call before capturing the stream into a CUDA graph.
 #include <mutex>
 
 #include "pauli.h"
@@ -56,8 +61,21 @@ cudaError_t scratch_for_current_device(StaticScratch** out) {
   return cudaSuccess;
 }
 
-// Host staging of the matrix table: static storage, one per thread, reused by every call.
-thread_local PlanMat t_table[kStaticMaxBatch];
+// The matrix table as a kernel parameter.
+struct StaticTableArgs {
+  PlanMat mats[kStaticMaxBatch];
+};
+static_assert(sizeof(StaticTableArgs) + 16 <= 32764, "the table fits the kernel parameter limit");
+
+// Copies the table into the array and clears the control block (one thread per entry).
+__global__ void static_table_store(const __grid_constant__ StaticTableArgs a, int batch, StaticScratch* s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < batch) s->mats[i] = a.mats[i];
+  if (i == 0) s->ctrl = PlanCtrl{0, 0, 0, 0};
+}
+
+// Host staging of the table, one per thread (its contents are copied at the launch).
+thread_local StaticTableArgs t_args;
 thread_local int t_order[kStaticMaxBatch];
 
 }  // namespace
@@ -85,14 +103,15 @@ int static_batch_launch(const void* const* G_list, const int* N_list, int batch,
   long long items = 0;
   for (int i = 0; i < batch; ++i) {
     const int b = t_order[i], N = N_list[b];
-    t_table[i] = PlanMat{G_list[b], out_list[b], N, (int)items};
+    t_args.mats[i] = PlanMat{G_list[b], out_list[b], N, (int)items};
     items += N >= nmin ? (long long)((1ull << (2 * N)) >> 13) : 1ll;
   }
   StaticScratch* scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(scratch->mats, t_table, (size_t)batch * sizeof(PlanMat), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&scratch->ctrl, 0, sizeof(PlanCtrl), s);
+  if (e == cudaSuccess) {
+    static_table_store<<<(batch + 255) / 256, 256, 0, s>>>(t_args, batch, scratch);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = launch_plan(nullptr, (int)items, scratch->mats, &scratch->ctrl, c64, 13, 0, s, batch);
   if (e != cudaSuccess) {
     *what = "static batch launch";

@@ -21,8 +21,9 @@ cudaError_t tiled_launch_re_c128_r4(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_re_c64_r3(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_re_c64_r4(const void*, int, int, void*, cudaStream_t);
 
+// The first buffer of a stream is sized for every N, so that it is never replaced.
 cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out) {
-  return stream_workspace(kWorkspaceTiled, st, bytes, kTiledCtrlBytes, out);
+  return stream_workspace(kWorkspaceTiled, st, bytes, tiled_workspace_max_bytes(), kTiledCtrlBytes, out);
 }
 
 namespace {

@@ -26,6 +26,9 @@ constexpr size_t kTiledCtrlBytes = 2048;  // control block, padded; the slots fo
 static_assert(sizeof(TiledCtrl) <= kTiledCtrlBytes, "control block fits its padding");
 
 bool tiled_supported(int N);
+// Scratch bytes a tiled launch at N needs (0 when N has no tiled kernel), and the most over N.
+size_t tiled_workspace_bytes(int N);
+size_t tiled_workspace_max_bytes();
 // rb = log2 of the elements per consumer thread: 3 (512 consumer threads) or 4 (256).
 // re: store only the real parts, into an array of reals (Hermitian decomposition).
 cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st,

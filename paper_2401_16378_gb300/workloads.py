@@ -71,6 +71,14 @@ def integer_complex(N: int, seed: int, lo: int = -8, hi: int = 8, dtype=np.compl
     return (re + 1j * im).astype(dtype)
 
 
+def gaussian_coefficients(N: int, seed: int, dtype=np.complex128) -> np.ndarray:
+    """4^N complex coefficients with real and imaginary parts i.i.d. N(0, 1) (real part first)."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal(4 ** N)
+    im = rng.standard_normal(4 ** N)
+    return (re + 1j * im).astype(dtype)
+
+
 def special_indices(N: int) -> np.ndarray:
     """0, 1, 2, 3, all-X, all-Y, all-Z coefficient indices (deduplicated, sorted)."""
     all_x = sum(1 << (2 * t) for t in range(N))

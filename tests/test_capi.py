@@ -161,6 +161,51 @@ def test_list_and_plan_argument_errors(lib):
     assert lib.pauli_decompose_list(None, None, 0, C128, None, 0, None) == OK
 
 
+def _ptr_list(vals):
+    arr = (ctypes.c_void_p * len(vals))(*vals)
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def test_compose_batched_rejects_bad_arguments(lib):
+    cs, k1 = _ptr_list([A, A + 0x100000])
+    gs, k2 = _ptr_list([B, B + 0x100000])
+    ns = (ctypes.c_int * 2)(3, 5)
+    assert lib.pauli_compose_batched(cs, ns, 2, 7, gs, 0, None) == DTYPE
+    assert lib.pauli_compose_batched(cs, ns, -1, C128, gs, 0, None) == ARG
+    assert lib.pauli_compose_batched(cs, ns, 0, C128, gs, 0, None) == OK  # nothing to do
+    assert lib.pauli_compose_batched(None, ns, 2, C128, gs, 0, None) == NULL
+    assert lib.pauli_compose_batched(cs, ns, 2, C128, gs, 65, None) == ARG
+    bad = (ctypes.c_int * 2)(3, 12)
+    assert lib.pauli_compose_batched(cs, bad, 2, C128, gs, 0, None) == ARG  # N above 11
+    assert b"11" in lib.pauli_last_error()
+    alias, k3 = _ptr_list([A, B])
+    assert lib.pauli_compose_batched(cs, ns, 2, C128, alias, 0, None) == ALIAS  # entry 0: c and G overlap
+    unal, k4 = _ptr_list([A + 8, A + 0x100000])
+    assert lib.pauli_compose_batched(unal, ns, 2, C128, gs, 0, None) == ALIGN
+
+
+def test_workspace_entry_points_reject_bad_arguments(lib):
+    n = ctypes.c_size_t(123)
+    assert lib.pauli_decompose_workspace_size(14, 1, C128, 0, None) == NULL
+    assert lib.pauli_decompose_workspace_size(0, 1, C128, 0, ctypes.byref(n)) == ARG
+    assert lib.pauli_decompose_workspace_size(14, 0, C128, 0, ctypes.byref(n)) == ARG
+    assert lib.pauli_decompose_workspace_size(14, 1, 3, 0, ctypes.byref(n)) == DTYPE
+    # the built-in shape at N = 14 is the tiled kernel: it needs scratch; PLAIN and N = 10 need none
+    assert lib.pauli_decompose_workspace_size(14, 1, C128, 0, ctypes.byref(n)) == OK and n.value > (1 << 20)
+    need = n.value
+    assert lib.pauli_decompose_workspace_size(14, 1, C128, 1, ctypes.byref(n)) == OK and n.value == 0
+    assert lib.pauli_decompose_workspace_size(10, 1, C128, 0, ctypes.byref(n)) == OK and n.value == 0
+    assert lib.pauli_decompose_workspace_size(14, 2000, C128, 0, ctypes.byref(n)) == OK and n.value == 0
+    W = 0x40000000
+    assert lib.pauli_decompose_ws(P(A), 14, 1, C128, P(B), 0, None, need, None) == ALIAS  # G, out overlap
+    G14, O14 = 0x100000000, 0x300000000  # 4 GiB each, apart
+    assert lib.pauli_decompose_ws(P(G14), 14, 1, C128, P(O14), 0, None, need, None) == NULL
+    assert lib.pauli_decompose_ws(P(G14), 14, 1, C128, P(O14), 0, P(W + 16), need, None) == ALIGN
+    assert lib.pauli_decompose_ws(P(G14), 14, 1, C128, P(O14), 0, P(W), need - 1, None) == ARG
+    assert lib.pauli_decompose_ws(P(G14), 14, 1, C128, P(O14), 0, P(G14 + 4096), need, None) == ALIAS
+    assert lib.pauli_workspace_status(None, None) == NULL
+
+
 def test_injected_launch_failure_is_reported(lib):
     lib.pauli_debug_fail_next_launches(1)
     assert lib.pauli_decompose(P(A), 4, 1, C128, P(B), 0, None) == CUDA

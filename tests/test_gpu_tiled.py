@@ -171,3 +171,76 @@ def test_tiled_variant_is_decompose_only():
         pg.set_variant(14, torch.complex128, "compose", "tiled8")
     with pytest.raises(pg.PauliError, match="UNSUPPORTED"):
         pg.set_variant(11, torch.complex128, "decompose", "tiled8")
+
+
+def _workspace(N, dtype, count=1):
+    nbytes = pg.decompose_workspace_size(N, count, dtype)
+    assert nbytes > 0
+    return torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+
+
+@pytest.mark.parametrize("N", [12, 13])
+def test_decompose_ws_matches_library_workspace(N):
+    """Caller-provided scratch gives the same bits as the library's per-stream buffer."""
+    dtype = torch.complex128
+    G = workloads.gaussian_complex(N, 3100 + N)
+    Gd = dev(G)
+    pg.set_variant(N, dtype, "decompose", "tiled16")
+    try:
+        ws = _workspace(N, dtype)
+        a = pg.decompose_ws(Gd, ws, method="xordiag")
+        pg.workspace_status(ws)
+        b = pg.decompose(Gd, method="xordiag")
+        pg.stream_status()
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        with pytest.raises(pg.PauliError, match="ERR_ARG"):
+            pg.decompose_ws(Gd, ws[: ws.numel() - 256], method="xordiag")  # too small: rejected, nothing runs
+    finally:
+        pg.set_variant(N, dtype, "decompose", "default")
+    idx = workloads.sample_indices(N, 3200 + N, k=256)
+    assert_close(host(a)[idx.astype(np.int64)], oracle.decompose_at(G, idx), np.max(np.abs(G)), dtype)
+
+
+def test_decompose_ws_first_call_on_a_stream_under_graph_capture():
+    """With caller scratch nothing is allocated, so the first tiled call on a fresh stream can be
+    captured; the graph replays it."""
+    N, dtype = 12, torch.complex128
+    G = workloads.gaussian_complex(N, 3300)
+    Gd = dev(G)
+    pg.set_variant(N, dtype, "decompose", "tiled16")
+    try:
+        want = pg.decompose(Gd, method="xordiag")  # kernel set-up outside the capture
+        pg.stream_status()
+        ws = _workspace(N, dtype)
+        out = torch.full_like(want, float("nan"))
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        with torch.cuda.graph(graph, stream=side):
+            pg.decompose_ws(Gd, ws, out=out, method="xordiag")
+        assert torch.isnan(out).all().item()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, want)
+        pg.workspace_status(ws)
+    finally:
+        pg.set_variant(N, dtype, "decompose", "default")
+
+
+def test_release_workspaces_then_decompose_again():
+    N, dtype = 12, torch.complex128
+    G = workloads.gaussian_complex(N, 3400)
+    Gd = dev(G)
+    s = torch.cuda.Stream()
+    pg.set_variant(N, dtype, "decompose", "tiled16")
+    try:
+        with torch.cuda.stream(s):
+            a = pg.decompose(Gd, method="xordiag")
+            pg.release_workspaces()  # frees this stream's ring after synchronising it
+            b = pg.decompose(Gd, method="xordiag")  # allocates afresh
+            pg.stream_status()
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+    finally:
+        pg.set_variant(N, dtype, "decompose", "default")

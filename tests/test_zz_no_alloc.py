@@ -2,11 +2,14 @@
 
 Callers that cannot allocate device memory -- a fixed memory budget, or an allocator that
 must not be re-entered at that point -- use this entry point instead of a plan. It keeps its
-work counter and matrix table in a fixed array in the library's device memory. This test
-calls it through the C ABI twice in a row with different batches (the second call must not
-see the first call's state) and compares every output with the existing entry points: the
+work counter and matrix table in a fixed array in the library's device memory. These tests
+call it through the C ABI twice in a row with different batches (the second call must not
+see the first call's state) and compare every output with the existing entry points -- the
 plan (same per-item arithmetic, bit for bit) and one launch per matrix (within the usual
-tolerance, since small matrices there use the plain FP64 sum).
+tolerance, since small matrices there use the plain FP64 sum) -- and a seeded sample of each
+matrix's coefficients with the CPU oracle. A captured call must replay its own batch: the
+table travels as a kernel parameter, so a later direct call with another batch does not
+change what the graph decomposes.
 """
 import ctypes
 
@@ -14,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2401_16378_gb300 as pg
 from paper_2401_16378_gb300 import _lib, workloads
 
@@ -29,7 +33,7 @@ def _ptrs(ts):
     return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
 
 
-def _static_call(Gd, outs, Ns, dtype):
+def _static_enqueue(Gd, outs, Ns, dtype):
     lib = _lib.load()
     gp, k1 = _ptrs(Gd)
     op, k2 = _ptrs(outs)
@@ -37,7 +41,23 @@ def _static_call(Gd, outs, Ns, dtype):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     st = lib.pauli_decompose_batch_static(gp, narr, len(Ns), CODE[dtype], op, stream)
     assert st == 0, lib.pauli_last_error()
+
+
+def _static_call(Gd, outs, Ns, dtype):
+    _static_enqueue(Gd, outs, Ns, dtype)
     torch.cuda.synchronize()
+
+
+def _check_oracle(mats, outs, dtype, seed):
+    """A seeded sample of every matrix's coefficients against the CPU oracle (all of them for N <= 4)."""
+    for b, (G, o) in enumerate(zip(mats, outs)):
+        N = G.shape[0].bit_length() - 1
+        idx = (np.arange(4 ** N, dtype=np.uint64) if N <= 4
+               else workloads.sample_indices(N, seed * 7919 + b, k=48))
+        ref = oracle.decompose_at(G, idx)
+        got = o.cpu().numpy()[idx.astype(np.int64)]
+        err = np.max(np.abs(got - ref))
+        assert err <= TOL[dtype] * np.max(np.abs(G)), (b, N, err)
 
 
 def _batch(seed, n, dtype):
@@ -67,6 +87,40 @@ def test_static_batch_matches_existing_entry_points_twice(dtype):
             assert torch.equal(o, p)
             err = torch.max(torch.abs(o - q)).item()
             assert err <= TOL[dtype] * np.max(np.abs(G))
+        _check_oracle(mats, outs, dtype, seed)
+
+
+def test_static_batch_graph_replays_its_own_batch():
+    """Capture one call, make a direct call with another batch, then replay: each output set must
+    hold its own batch's coefficients (oracle sample), because the table is a kernel parameter."""
+    dtype = torch.complex128
+    NsA, matsA = _batch(21, 29, dtype)
+    NsB, matsB = _batch(22, 41, dtype)
+    GA = [torch.from_numpy(G).cuda() for G in matsA]
+    GB = [torch.from_numpy(G).cuda() for G in matsB]
+    outA = [torch.full((4 ** int(N),), float("nan"), dtype=dtype, device="cuda") for N in NsA]
+    outB = [torch.full((4 ** int(N),), float("nan"), dtype=dtype, device="cuda") for N in NsB]
+    _static_call(GB, outB, NsB, dtype)  # the first call on the device: before any capture
+    for o in outB:
+        o.fill_(float("nan"))
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=side):
+        _static_enqueue(GA, outA, NsA, dtype)
+    assert all(torch.isnan(o).all().item() for o in outA)  # capture enqueues nothing
+    _static_call(GB, outB, NsB, dtype)  # a direct call with another table after the capture
+    graph.replay()
+    torch.cuda.synchronize()
+    _check_oracle(matsA, outA, dtype, 21)
+    _check_oracle(matsB, outB, dtype, 22)
+    graph.replay()  # a second replay after nothing else: same result, bit for bit
+    again = [o.clone() for o in outA]
+    for o in outA:
+        o.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, o) for a, o in zip(again, outA))
 
 
 def test_static_batch_rejects_oversized_batch():
