@@ -40,7 +40,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", "--qubits", dest="n", type=int, default=14, help="qubits of the timed workload")
     p.add_argument("--quick", action="store_true", help="skip the secondary forms")
-    p.add_argument("--variant", default="default", choices=["default", "unit8192", "unit4096", "unit4096x8", "unit8192x8"],
+    p.add_argument("--variant", default="default", choices=["default", "unit8192", "unit4096", "unit4096x8", "unit8192x8", "tiled8", "tiled16",
+                            "twostage"],
                    help="XOR-diagonal launch shape of the timed step")
     p.add_argument("--profile", action="store_true",
                    help="only warm-up + timed kernel launches (for ncu); prints the step time")

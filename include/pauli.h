@@ -68,8 +68,8 @@ typedef enum {
  * contiguously at G into 4^N coefficients each, stored contiguously at out.
  *   out[k * 4^N + n] = c_n of matrix k = 2^-N Tr(P_n G_k)              Eq. (4), via Eq. (13).
  * dtype applies to both G and out. method: pauli_method.
- * With PAULI_XORDIAG at N = 13 and 14 the built-in launch shape is a tiled one (see
- * PAULI_VARIANT_TILED8 below) that needs a scratch ring between its two stages. This entry point
+ * With PAULI_XORDIAG at N = 13 and 14 the built-in launch shape is a two-stage one (see
+ * PAULI_VARIANT_TWOSTAGE below) that needs a scratch ring between its two stages. This entry point
  * takes it from a library-owned buffer per (device, stream), allocated with cudaMalloc at the
  * first tiled call on that pair, sized for every N so that it is never replaced, and kept until
  * pauli_release_workspaces: make the first such call on a stream before capturing that stream
@@ -308,16 +308,27 @@ void pauli_plan_destroy(pauli_plan* plan);
  *                           the other N - 6. One persistent, warp-specialised launch (a copy
  *                           warp feeding 512 compute threads, 8 elements each, through a ring
  *                           of shared-memory buffers). The scratch (S x 2^(N+10) bytes plus
- *                           a little, S = 6, 5, 3 slots at N = 12, 13, 14) is allocated with cudaMalloc at the first call on each
- *                           (device, stream) pair and kept until the process exits: make that
- *                           first call before capturing the stream into a graph. Calls on one
- *                           stream are ordered by the stream; calls on different streams get
- *                           different scratch.
+ *                           a little, S = 6, 5, 3 slots at N = 12, 13, 14) comes from the
+ *                           library's buffer for the (device, stream) pair, or from the caller
+ *                           (pauli_decompose_ws). Calls on one stream are ordered by the stream;
+ *                           calls on different streams get different library buffers.
  * PAULI_VARIANT_TILED16:    the same with two groups of 256 compute threads of 16 elements
  *                           each, working on alternate buffers.
- * All variants compute bit-identical complex128 results, except that the tiled ones re-scale
+ * PAULI_VARIANT_TWOSTAGE:   decomposition only, N 12..14 (the built-in choice at N = 13, 14): the
+ *                           same two stages, tiles and scratch ring, with every compute warp
+ *                           running its 512 elements of a work item on its own (its own part of
+ *                           the tile, its own copy of the stage-2 data, exchanges within the warp)
+ *                           and no barrier between the warps of an item. complex64 runs compensated
+ *                           FP32: each value split into a high part on a per-mask power-of-two
+ *                           grid, whose sums are exact, and a low part that carries the rounding
+ *                           errors (error-free Fast2Sum against the grid's anchor); inputs above
+ *                           2^(127 - N) in magnitude overflow. Scratch as for the tiled variants;
+ *                           pauli_decompose_workspace_size reports it.
+ * All variants compute bit-identical complex128 results, except that the two-stage ones re-scale
  * partial sums between the stages (an extra truncation below the class quantum, well inside
- * the accuracy bound of pauli_decompose); they differ otherwise only in speed. The choice is
+ * the accuracy bound of pauli_decompose; the three two-stage variants agree with each other bit
+ * for bit); they differ otherwise only in speed. complex64 results of different variants agree
+ * to within the accuracy bound, not bit for bit. The choice is
  * process-wide per (N, dtype, op): op 0 = decompose, 1 = compose, for calls on one matrix
  * (count = 1); op 2 = decompose, 3 = compose, for calls on a batch (count > 1), where the
  * units of many matrices fill the GPU and a different shape can win. Variant 0 restores the
@@ -330,6 +341,7 @@ void pauli_plan_destroy(pauli_plan* plan);
 #define PAULI_VARIANT_UNIT8192X8 4
 #define PAULI_VARIANT_TILED8 5
 #define PAULI_VARIANT_TILED16 6
+#define PAULI_VARIANT_TWOSTAGE 7
 int pauli_set_variant(int N, int dtype, int op, int variant);
 /* The variant in effect for (N, dtype, op), or 0 when PAULI_XORDIAG has none for N. */
 int pauli_get_variant(int N, int dtype, int op);

@@ -484,7 +484,7 @@ def decompose_weighted_norm_autograd(G: torch.Tensor, w: torch.Tensor, method="a
 
 
 VARIANTS = {"default": 0, "unit8192": 1, "unit4096": 2, "unit4096x8": 3, "unit8192x8": 4, "tiled8": 5,
-            "tiled16": 6}
+            "tiled16": 6, "twostage": 7}
 
 
 OPS = {"decompose": 0, "compose": 1, "decompose_batched": 2, "compose_batched": 3}

@@ -31,8 +31,9 @@ _DT = {"c128": torch.complex128, "c64": torch.complex64}
 _DT_CODE = {"c128": _lib.PAULI_C128, "c64": _lib.PAULI_C64}
 _OPS = {"decompose": 0, "compose": 1, "decompose_batched": 2, "compose_batched": 3}
 BATCH_ELEMENTS = 1 << 26  # a tuning batch holds about this many elements (1 GiB of complex128)
-VARIANT_RANGE = {1: (7, 15), 2: (6, 14), 3: (6, 14), 4: (7, 15), 5: (12, 14), 6: (12, 14)}  # variant -> N range
-DECOMPOSE_ONLY = {5, 6}  # the two-stage tiled variants
+VARIANT_RANGE = {1: (7, 15), 2: (6, 14), 3: (6, 14), 4: (7, 15), 5: (12, 14), 6: (12, 14),
+                 7: (12, 14)}  # variant -> N range
+DECOMPOSE_ONLY = {5, 6, 7}  # the two-stage variants
 
 
 def _gpu_name() -> str:

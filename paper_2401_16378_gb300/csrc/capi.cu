@@ -178,7 +178,8 @@ int decompose_workspace_bytes(int N, long long count, int dtype, int method, siz
   if ((st = resolve_method(method, N, &m))) return st;
   if (m != PAULI_XORDIAG || !pauli::tiled_supported(N) || count > 1024) return PAULI_OK;
   const int v = pauli::xordiag_get_variant(N, dtype == PAULI_C64, false, count > 1);
-  if (v == pauli::kVariantTiled8 || v == pauli::kVariantTiled16) *bytes = pauli::tiled_workspace_bytes(N);
+  if (v == pauli::kVariantTiled8 || v == pauli::kVariantTiled16 || v == pauli::kVariantTwoStage)
+    *bytes = pauli::tiled_workspace_bytes(N);
   return PAULI_OK;
 }
 

@@ -32,6 +32,7 @@ constexpr int kVariantUnit12x8 = 3;  // 4096-element units, 512 threads x 8 elem
 constexpr int kVariantUnit13x8 = 4;  // 8192-element units, 1024 threads x 8 elements
 constexpr int kVariantTiled8 = 5;    // two-stage tiled decomposition (tiled.cu), 512 consumers x 8 elements
 constexpr int kVariantTiled16 = 6;   // two-stage tiled decomposition, 256 consumers x 16 elements
+constexpr int kVariantTwoStage = 7;  // two-stage decomposition with warp-independent consumers
 bool xordiag_supported(int N);
 bool xordiag_variant_supported(int variant, int N, bool compose);
 // batched: the choice for calls with count > 1 (kept apart from the one-matrix choice).

@@ -20,6 +20,11 @@ cudaError_t tiled_launch_re_c128_r3(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_re_c128_r4(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_re_c64_r3(const void*, int, int, void*, cudaStream_t);
 cudaError_t tiled_launch_re_c64_r4(const void*, int, int, void*, cudaStream_t);
+cudaError_t twostage_launch_c128(const void*, int, int, void*, cudaStream_t);
+cudaError_t twostage_launch_c64(const void*, int, int, void*, cudaStream_t);
+cudaError_t twostage_launch_re_c128(const void*, int, int, void*, cudaStream_t);
+cudaError_t twostage_launch_re_c64(const void*, int, int, void*, cudaStream_t);
+size_t twostage_workspace_bytes_c128(int N);
 
 // The first buffer of a stream is sized for every N, so that it is never replaced.
 cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out) {
@@ -65,6 +70,36 @@ cudaError_t tiled_tensor_map(CUtensorMap* map, const void* G, int N, int count, 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t scratch_tensor_map(CUtensorMap* map, void* base, long long rows, int row_words, int box_words,
+                               int box_rows) {
+  EncodeTiled fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)row_words, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)row_words * 8u};
+  const cuuint32_t box[2] = {(cuuint32_t)box_words, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 4D map of stage-2 chunks: (words of one warp's transforms, tile R, warp slice, chunk) over the
+// dense [chunk][R][slice][words] scratch; a box of one chunk lands as [slice][R][words].
+cudaError_t scratch_tensor_map4(CUtensorMap* map, void* base, int chunks, int nr, int slice_words) {
+  auto fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t row = (cuuint64_t)slice_words * 8u * 8u;  // bytes of one R row: 8 slices
+  const cuuint64_t dims[4] = {(cuuint64_t)slice_words, (cuuint64_t)nr, 8u, (cuuint64_t)chunks};
+  const cuuint64_t strides[3] = {row, (cuuint64_t)slice_words * 8u, row * (cuuint64_t)nr};
+  const cuuint32_t box[4] = {(cuuint32_t)slice_words, (cuuint32_t)nr, 8u, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 namespace {
 std::atomic<bool> g_stall_next{false};
 }  // namespace
@@ -76,6 +111,12 @@ bool tiled_supported(int N) { return N >= 12 && N <= 14; }
 
 cudaError_t launch_tiled(const void* G, int N, int count, bool c64, void* out, int rb, cudaStream_t st, bool re) {
   if (!tiled_supported(N)) return cudaErrorNotSupported;
+  if (rb == 0) {  // the warp-independent two-stage kernel
+    using Fn = cudaError_t (*)(const void*, int, int, void*, cudaStream_t);
+    static const Fn ts_table[2][2] = {{twostage_launch_c128, twostage_launch_c64},
+                                      {twostage_launch_re_c128, twostage_launch_re_c64}};
+    return ts_table[re][c64](G, N, count, out, st);
+  }
   using Fn = cudaError_t (*)(const void*, int, int, void*, cudaStream_t);
   static const Fn table[2][2][2] = {  // [re][c64][rb == 4]
       {{tiled_launch_c128_r3, tiled_launch_c128_r4}, {tiled_launch_c64_r3, tiled_launch_c64_r4}},

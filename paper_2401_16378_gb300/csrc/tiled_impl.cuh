@@ -325,6 +325,7 @@ __device__ void releaser(TiledCtrl* ws, Shared& sh) {
     if (r == -2) break;
     // every consumer warp's stores precede its arrival; the release makes them visible first
     if (r >= 0) red_release_add(&ws->s1_done[r], 1);
+    __threadfence_block();  // the read of rel_slot[buf] completes before its slot may be rewritten
     *released = use + 1;
   }
 }
@@ -547,6 +548,7 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
         }
         __nanosleep(64);
       }
+      __threadfence_block();  // the release warp's read of rel_slot[] precedes this group's write of it
       ok = ok && wait_phase(full, parity, &ws->status);
       if (ok) sh.waited_use[buf] = use;
       sh.ok[g] = ok;

@@ -49,10 +49,14 @@ cudaError_t xordiag_herm_upper_c64(int, const void*, long long, void*, cudaStrea
 
 namespace {
 
+bool is_tiled(int v) { return v == kVariantTiled8 || v == kVariantTiled16 || v == kVariantTwoStage; }
+// Consumer shape argument of launch_tiled: 3 / 4 = block-tiled kernel, 0 = warp-independent kernel.
+int tiled_rb(int v) { return v == kVariantTiled8 ? 3 : v == kVariantTiled16 ? 4 : 0; }
+
 bool variant_has(int variant, int N, bool compose) {
   if (variant == kVariantUnit13 || variant == kVariantUnit13x8) return N >= 7 && N <= 15;
   if (variant == kVariantUnit12 || variant == kVariantUnit12x8) return N >= 6 && N <= 14;
-  if (variant == kVariantTiled8 || variant == kVariantTiled16) return !compose && tiled_supported(N);
+  if (is_tiled(variant)) return !compose && tiled_supported(N);
   return false;
 }
 
@@ -63,14 +67,14 @@ constexpr long long kTiledMaxCount = 1024;
 // by the autotuner.
 int g_variant[2][2][2][17];
 
-// Built-in choice (measured on GB300): the two-stage tiled kernel for decompositions at
-// N = 13, 14 -- two groups of 16 elements per thread, except one group of 8 for complex64 at
-// N = 13 -- else single-pass units of 8192 (4096 below N = 7) elements; for batches of
-// matrices below N = 12, 4096-element units on two CTAs per SM (64 x N = 10: 0.46 instead of
+// Built-in choice (measured on GB300): the warp-independent two-stage kernel for decompositions
+// at N = 12..14 (N = 14: 2.40 ms complex128 and 2.10 ms complex64, against 2.60 and 3.12 ms for the
+// block-tiled kernel; N = 12: 0.186 / 0.143 ms against 0.186 / 0.176 ms single-pass), else single-pass units of 8192 (4096 below N = 7) elements; for batches
+// of matrices below N = 12, 4096-element units on two CTAs per SM (64 x N = 10: 0.46 instead of
 // 0.50 ms).
 int default_variant(int N, bool c64, bool compose, bool batched) {
-  if (!compose && N == 14) return kVariantTiled16;
-  if (!compose && N == 13) return c64 ? kVariantTiled8 : kVariantTiled16;
+  (void)c64;
+  if (!compose && N >= 12 && N <= 14) return kVariantTwoStage;
   if (batched && N < 12) return kVariantUnit12;
   return N >= 7 ? kVariantUnit13 : kVariantUnit12;
 }
@@ -97,16 +101,16 @@ cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, boo
                            cudaStream_t s, int variant) {
   if (!variant) {
     variant = xordiag_get_variant(N, c64, compose, count > 1);
-    if ((variant == kVariantTiled8 || variant == kVariantTiled16) &&
+    if (is_tiled(variant) &&
         (count > kTiledMaxCount || (reinterpret_cast<uintptr_t>(in) & 15u)))
       variant = single_pass_variant(N);
   }
   if (!variant_has(variant, N, compose)) return cudaErrorNotSupported;
-  if (variant == kVariantTiled8 || variant == kVariantTiled16) {
+  if (is_tiled(variant)) {
     // the bulk copies need 16-byte aligned sources: other G take the single-pass kernel
     if (count > kTiledMaxCount || (reinterpret_cast<uintptr_t>(in) & 15u))
       return launch_xordiag(in, N, count, c64, compose, scale_exp, out, s, single_pass_variant(N));
-    return launch_tiled(in, N, (int)count, c64, out, variant == kVariantTiled8 ? 3 : 4, s);
+    return launch_tiled(in, N, (int)count, c64, out, tiled_rb(variant), s);
   }
   if (c64)
     return compose ? xordiag_c64_compose(variant, N, in, count, scale_exp, out, s)
@@ -121,9 +125,8 @@ cudaError_t launch_xordiag(const void* in, int N, long long count, bool c64, boo
 cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, void* out, cudaStream_t s) {
   if (!xordiag_supported(N)) return cudaErrorNotSupported;
   const int v = xordiag_get_variant(N, c64, false, count > 1);
-  if ((v == kVariantTiled8 || v == kVariantTiled16) && tiled_supported(N) && count <= kTiledMaxCount &&
-      !(reinterpret_cast<uintptr_t>(in) & 15u))
-    return launch_tiled(in, N, (int)count, c64, out, v == kVariantTiled8 ? 3 : 4, s, true);
+  if (is_tiled(v) && tiled_supported(N) && count <= kTiledMaxCount && !(reinterpret_cast<uintptr_t>(in) & 15u))
+    return launch_tiled(in, N, (int)count, c64, out, tiled_rb(v), s, true);
   const bool unit4096 = (v == kVariantUnit12 || v == kVariantUnit12x8) && N <= 14;
   return c64 ? xordiag_re_decompose_c64(N, in, count, out, s, unit4096)
              : xordiag_re_decompose_c128(N, in, count, out, s, unit4096);
@@ -134,7 +137,7 @@ cudaError_t launch_xordiag_re(const void* in, int N, long long count, bool c64, 
 cudaError_t launch_xordiag_real(const void* in, int N, long long count, void* out, cudaStream_t s) {
   if (!xordiag_supported(N)) return cudaErrorNotSupported;
   const int v = xordiag_get_variant(N, false, false, count > 1);
-  if ((v == kVariantTiled8 || v == kVariantTiled16) && tiled_supported(N) && count <= kTiledMaxCount &&
+  if (is_tiled(v) && tiled_supported(N) && count <= kTiledMaxCount &&
       !(reinterpret_cast<uintptr_t>(in) & 15u))
     return tiled_launch_real_r4(in, N, (int)count, out, s);
   const bool unit4096 = (v == kVariantUnit12 || v == kVariantUnit12x8) && N <= 14;

@@ -72,12 +72,12 @@ def test_decompose_rejects_bad_arguments(lib):
     assert lib.pauli_set_variant(14, C128, 4, 1) == ARG
     assert lib.pauli_get_variant(10, C128, 0) == 1  # one matrix: 8192-element units
     assert lib.pauli_get_variant(10, C128, 2) == 2  # a batch: 4096-element units, two CTAs per SM
-    assert lib.pauli_get_variant(14, C128, 2) == 6
+    assert lib.pauli_get_variant(14, C128, 2) == 7
     assert lib.pauli_set_variant(14, C128, 3, 5) == UNSUP
     assert lib.pauli_get_variant(3, C128, 0) == 0
-    assert lib.pauli_get_variant(14, C128, 0) == 6  # decompose at N = 14: the tiled kernel
+    assert lib.pauli_get_variant(14, C128, 0) == 7  # decompose at N = 14: the two-stage kernel
     assert lib.pauli_get_variant(14, C128, 1) == 1  # compose: single-pass 8192-element units
-    assert lib.pauli_get_variant(12, C128, 0) == 1
+    assert lib.pauli_get_variant(12, C128, 0) == 7
     assert lib.pauli_set_variant(14, C128, 1, 5) == UNSUP  # tiled is decompose-only
 
 

@@ -1,4 +1,4 @@
-"""GPU parity of the two-stage tiled decomposition (PAULI_VARIANT_TILED8 / TILED16).
+"""GPU parity of the two-stage decompositions (PAULI_VARIANT_TILED8 / TILED16 / TWOSTAGE).
 
 Stage 1 transforms 64 XY-masks x 64 rows per tile with a per-(class, tile) fixed-point
 scale, stage 2 re-scales the tiles of each class to the class maximum and finishes the
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {torch.complex128: 1e-12, torch.complex64: 2e-6}
 NP = {torch.complex128: np.complex128, torch.complex64: np.complex64}
-TILED = ("tiled8", "tiled16")
+TILED = ("tiled8", "tiled16", "twostage")
 
 
 def dev(a):
@@ -92,11 +92,12 @@ def test_tiled_rescaling_across_binades_and_zero_tiles(variant):
     assert_close(got[idx.astype(np.int64)], oracle.decompose_at(G, idx), np.max(np.abs(G)), torch.complex128)
 
 
-def test_tiled_nonfinite_entry_gives_nan_for_its_mask_only():
+@pytest.mark.parametrize("variant", ("tiled8", "twostage"))
+def test_tiled_nonfinite_entry_gives_nan_for_its_mask_only(variant):
     N = 12
     G = workloads.gaussian_complex(N, 2500)
     G[700, 3001] = np.inf
-    got = run_tiled(dev(G), N, torch.complex128, "tiled8")
+    got = run_tiled(dev(G), N, torch.complex128, variant)
     n_all = np.arange(4 ** N, dtype=np.int64)
     even = np.zeros_like(n_all)
     odd = np.zeros_like(n_all)
@@ -108,14 +109,15 @@ def test_tiled_nonfinite_entry_gives_nan_for_its_mask_only():
     assert not np.any(np.isnan(got[~mask]))
 
 
+@pytest.mark.parametrize("variant", ("tiled8", "twostage"))
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
-def test_tiled_batch_and_repeated_launches(dtype):
+def test_tiled_batch_and_repeated_launches(dtype, variant):
     """count = 3 matrices in one launch (blocks of later matrices reuse ring slots), then the
     same launch twice more: identical results every time."""
     N = 12
     Gs = np.stack([workloads.gaussian_complex(N, 2600 + b) for b in range(3)]).astype(NP[dtype])
     Gd = dev(Gs)
-    pg.set_variant(N, dtype, "decompose_batched", "tiled8")
+    pg.set_variant(N, dtype, "decompose_batched", variant)
     try:
         outs = [host(pg.decompose(Gd, method="xordiag")) for _ in range(3)]
         pg.stream_status()
@@ -144,14 +146,15 @@ def test_tiled_c64_unaligned_matrix_takes_single_pass_path():
                  torch.complex64)
 
 
-def test_tiled_bounded_wait_reports_timeout_and_recovers():
+@pytest.mark.parametrize("variant", ("tiled16", "twostage"))
+def test_tiled_bounded_wait_reports_timeout_and_recovers(variant):
     """The stall hook makes the producers of the next tiled launch wait on a count that nothing
     raises; the bounded wait gives up, the launch ends early, pauli_stream_status reports
     PAULI_ERR_TIMEOUT once, and the next launch on the same stream is correct again."""
     N = 12
     G = workloads.gaussian_complex(N, 2800)
     Gd = dev(G)
-    pg.set_variant(N, torch.complex128, "decompose", "tiled16")
+    pg.set_variant(N, torch.complex128, "decompose", variant)
     try:
         pg.debug_stall_next_tiled()
         pg.decompose(Gd, method="xordiag")
@@ -179,13 +182,14 @@ def _workspace(N, dtype, count=1):
     return torch.empty(nbytes, dtype=torch.uint8, device="cuda")
 
 
+@pytest.mark.parametrize("variant", ("tiled16", "twostage"))
 @pytest.mark.parametrize("N", [12, 13])
-def test_decompose_ws_matches_library_workspace(N):
+def test_decompose_ws_matches_library_workspace(N, variant):
     """Caller-provided scratch gives the same bits as the library's per-stream buffer."""
     dtype = torch.complex128
     G = workloads.gaussian_complex(N, 3100 + N)
     Gd = dev(G)
-    pg.set_variant(N, dtype, "decompose", "tiled16")
+    pg.set_variant(N, dtype, "decompose", variant)
     try:
         ws = _workspace(N, dtype)
         a = pg.decompose_ws(Gd, ws, method="xordiag")
@@ -202,13 +206,14 @@ def test_decompose_ws_matches_library_workspace(N):
     assert_close(host(a)[idx.astype(np.int64)], oracle.decompose_at(G, idx), np.max(np.abs(G)), dtype)
 
 
-def test_decompose_ws_first_call_on_a_stream_under_graph_capture():
+@pytest.mark.parametrize("variant", ("tiled16", "twostage"))
+def test_decompose_ws_first_call_on_a_stream_under_graph_capture(variant):
     """With caller scratch nothing is allocated, so the first tiled call on a fresh stream can be
     captured; the graph replays it."""
     N, dtype = 12, torch.complex128
     G = workloads.gaussian_complex(N, 3300)
     Gd = dev(G)
-    pg.set_variant(N, dtype, "decompose", "tiled16")
+    pg.set_variant(N, dtype, "decompose", variant)
     try:
         want = pg.decompose(Gd, method="xordiag")  # kernel set-up outside the capture
         pg.stream_status()
@@ -244,3 +249,14 @@ def test_release_workspaces_then_decompose_again():
         assert torch.equal(a, b)
     finally:
         pg.set_variant(N, dtype, "decompose", "default")
+
+
+@pytest.mark.parametrize("N", [13, 14])
+def test_two_stage_variants_agree_bit_for_bit_in_complex128(N):
+    """The three two-stage kernels run the same int64 transform with the same per-tile scales:
+    identical complex128 coefficients."""
+    G = workloads.gaussian_complex(N, 3500 + N)
+    Gd = dev(G)
+    outs = [run_tiled(Gd, N, torch.complex128, v) for v in TILED]
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
