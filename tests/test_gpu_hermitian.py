@@ -39,20 +39,23 @@ def _check_against_oracle(G, got, N, dtype, k=None):
 
 
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
-@pytest.mark.parametrize("N", [1, 3, 5, 6, 8, 10, 12])
-def test_hermitian_matches_oracle_and_complex_path(N, dtype):
+@pytest.mark.parametrize("N,variant", [(1, None), (3, None), (5, None), (6, "same"), (8, "same"), (10, "same"),
+                                       (12, "same"), (12, "twostage")])
+def test_hermitian_matches_oracle_and_complex_path(N, variant, dtype):
+    """Real parts against the oracle, and bit for bit against the real part of the complex
+    decomposition in the same launch shape (both calls follow the decomposition's shape)."""
     G = workloads.hermitian_complex(N, 1600 + N).astype(NP[dtype])
     Gd = _dev(G)
-    got = pg.decompose_hermitian(Gd).cpu().numpy()
-    assert got.dtype == (np.float64 if dtype == torch.complex128 else np.float32)
-    _check_against_oracle(G, got, N, dtype, k=None if N <= 8 else 2048)
-    if N >= 6:
-        pg.set_variant(N, dtype, "decompose", _same_shape_variant(N))
+    if variant:
+        pg.set_variant(N, dtype, "decompose", _same_shape_variant(N) if variant == "same" else variant)
     try:
+        got = pg.decompose_hermitian(Gd).cpu().numpy()
         full = pg.decompose(Gd).cpu().numpy()
     finally:
-        if N >= 6:
+        if variant:
             pg.set_variant(N, dtype, "decompose", "default")
+    assert got.dtype == (np.float64 if dtype == torch.complex128 else np.float32)
+    _check_against_oracle(G, got, N, dtype, k=None if N <= 8 else 2048)
     np.testing.assert_array_equal(got, full.real)
     # Hermitian input: the dropped imaginary parts are rounding noise
     assert np.max(np.abs(full.imag)) <= TOL[dtype] * np.max(np.abs(G))

@@ -374,7 +374,7 @@ def test_transpose_flips_sign_of_odd_y_strings(N):
     b = host(pg.decompose(dev(np.ascontiguousarray(G.T))))
     k = oracle.y_count(np.arange(4 ** N), N)
     want = np.where(k % 2 == 1, -1.0, 1.0) * a
-    if 6 <= N <= 12:
+    if 6 <= N <= 11:
         np.testing.assert_array_equal(b, want)
-    else:
+    else:  # N = 12, 13: the two-stage kernel is the default there
         assert np.max(np.abs(b - want)) <= 2 * TOL[torch.complex128] * maxabs(G)

@@ -30,18 +30,19 @@ def _nonzero_part(c, N):
 def test_real_matches_oracle_and_complex_path(N):
     G = _real(N, 1800 + N)
     Gd = torch.from_numpy(G).cuda()
-    got = pg.decompose_real(Gd).cpu().numpy()
-    idx = np.arange(4 ** N, dtype=np.uint64) if N <= 6 else workloads.sample_indices(N, 1810 + N, k=512)
-    want = oracle.real_coefficients_at(G, idx)
-    assert np.max(np.abs(got[idx.astype(np.int64)] - want)) <= 1e-12 * np.max(np.abs(G)), N
-    # the complex path on G + 0i, same launch shape: its nonzero parts, bit for bit
+    # both paths follow the complex128 decomposition's launch shape: pin it for the two calls
     if 6 <= N <= 12:
         pg.set_variant(N, torch.complex128, "decompose", "unit8192" if N >= 7 else "unit4096")
     try:
+        got = pg.decompose_real(Gd).cpu().numpy()
         full = pg.decompose(Gd.to(torch.complex128), method="auto" if N >= 6 else "plain").cpu().numpy()
     finally:
         if 6 <= N <= 12:
             pg.set_variant(N, torch.complex128, "decompose", "default")
+    idx = np.arange(4 ** N, dtype=np.uint64) if N <= 6 else workloads.sample_indices(N, 1810 + N, k=512)
+    want = oracle.real_coefficients_at(G, idx)
+    assert np.max(np.abs(got[idx.astype(np.int64)] - want)) <= 1e-12 * np.max(np.abs(G)), N
+    # the complex path on G + 0i, same launch shape: its nonzero parts, bit for bit
     np.testing.assert_array_equal(got, _nonzero_part(full, N))
 
 
