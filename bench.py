@@ -45,8 +45,15 @@ def parse():
                    help="XOR-diagonal launch shape of the timed step")
     p.add_argument("--profile", action="store_true",
                    help="only warm-up + timed kernel launches (for ncu); prints the step time")
+    p.add_argument("--dtype", default="c128", choices=["c128", "c64"],
+                   help="element type of the --profile launches (the timed step is complex128)")
+    p.add_argument("--profile-batch", type=int, default=0,
+                   help="with --profile: launch the batched plan over the first B matrices of the "
+                        "uneven-N batch instead of the N-qubit decomposition")
+    p.add_argument("--hermitian", action="store_true",
+                   help="with --profile-batch: the Hermitian (upper-triangle, real output) plan")
     p.add_argument("--forms-only", default="",
-                   help="comma list of secondary forms (n6, n12, c64, batched, adjoint) to run alone, "
+                   help="comma list of secondary forms (n6, n12, c64, batched, adjoint, xhi) to run alone, "
                         "without the timed step; prints their JSON")
     return p.parse_args()
 
@@ -71,8 +78,9 @@ def measured_peak_hbm():
 
 def source_hash():
     h = hashlib.sha256()
-    # the device code of the timed kernel (tiled_kernel<14, 4, ArC128>) and what it includes
-    for name in ("tiled_impl.cuh", "tiled.h", "tiled_c128_r4.cu", "xordiag_impl.cuh", "common.cuh"):
+    # the device code of the timed kernel (the two-stage twostage_kernel at N 12..14) and what it includes
+    for name in ("twostage_impl.cuh", "ptx.cuh", "c64x.cuh", "twostage_c128.cu", "twostage_c64.cu", "tiled.h",
+                 "xordiag_impl.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2401_16378_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -154,21 +162,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_rate(G, N, seconds_target, seed=4242):
-    """Oracle coefficients per second on a bounded random sample of the workload."""
+def oracle_rate(G, N, seconds_target, seed=4242, impl=None):
+    """Coefficients per second of a CPU implementation (default: the oracle) on a bounded random
+    sample of the workload."""
     import oracle
     from paper_2401_16378_gb300 import workloads
 
-    threads = oracle.default_threads()
+    impl = impl or oracle
+    threads = impl.default_threads()
     probe = workloads.sample_indices(N, seed, k=max(16, threads), with_special=False)
     t0 = time.perf_counter()
-    oracle.decompose_at(G, probe)
+    impl.decompose_at(G, probe)
     dt = time.perf_counter() - t0
-    k = int(max(len(probe), min(1 << 20, len(probe) * seconds_target / max(dt, 1e-6))))
-    idx = workloads.sample_indices(N, seed + 1, k=k, with_special=False)
-    t0 = time.perf_counter()
-    oracle.decompose_at(G, idx)
-    dt = time.perf_counter() - t0
+    k = len(probe)
+    for attempt in range(3):  # the probe underestimates the rate (thread start-up): rescale once more
+        k = int(max(len(probe), min(1 << 22, k * seconds_target / max(dt, 1e-6))))
+        idx = workloads.sample_indices(N, seed + 1 + attempt, k=k, with_special=False)
+        t0 = time.perf_counter()
+        impl.decompose_at(G, idx)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds_target or k == 1 << 22:
+            break
     return k / dt, k, dt, threads
 
 
@@ -275,7 +289,7 @@ def run_ours(args):
 
     if args.forms_only:
         only = set(args.forms_only.split(","))
-        G14 = workloads.gaussian_complex(14, workloads.SEEDS["n14"]) if "c64" in only else None
+        G14 = workloads.gaussian_complex(14, workloads.SEEDS["n14"]) if only & {"c64", "xhi"} else None
         forms = secondary_forms(pg, workloads, dev, torch.cuda.current_stream(dev), G14, only=only)
         print(json.dumps({"forms": forms}), flush=True)
         return
@@ -295,12 +309,19 @@ def run_ours(args):
     def step():
         pg.decompose(G, out=out, method="xordiag")
 
+    if args.profile and args.profile_batch > 0:
+        profile_plan(pg, workloads, dev, stream, args)
+        return
     if args.profile:
+        if args.dtype == "c64":
+            G, out = G.to(torch.complex64), torch.empty(ncoef, dtype=torch.complex64, device=dev)
+            if args.variant != "default":
+                pg.set_variant(N, torch.complex64, "decompose", args.variant)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize(dev)
         ms = event_time(step, args.steps, stream)
-        print(json.dumps({"profile": True, "N": N, "ms_per_step": ms}), flush=True)
+        print(json.dumps({"profile": True, "N": N, "dtype": args.dtype, "ms_per_step": ms}), flush=True)
         return
 
     def barrier():
@@ -383,13 +404,20 @@ def run_ours(args):
     rate, k, dt, cores = oracle_rate(G_h, N, seconds_target=12.0)
     cpu = {"value": rate, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
            "sample": f"{k} seeded random coefficients of the N={N} workload in {dt:.1f} s (Eq. (13), O(2^N) each)"}
+    from oracle import gray
+
+    grate, gk, gdt, gcores = oracle_rate(G_h, N, seconds_target=8.0, impl=gray)
+    cpu_gray = {"value": grate, "unit": "coeffs/s", "cores": gcores, "kind": "gray_code",
+                "sample": f"{gk} seeded random coefficients of the N={N} workload in {gdt:.1f} s",
+                "what": "the paper's CPU algorithm (Sec. 3): Eq. (13) in Gray-code order with the lambda recurrence "
+                        "of Eq. (14), plain FP64 sums, C + OpenMP; a second, faster CPU baseline (not the checker)"}
 
     line = {"metric": metric_name(N), "value": value,
             "unit": "coeffs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": workload_config(N, world),
-            "roofline": roofline, "cpu_baseline": cpu,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_gray_code": cpu_gray,
             "e2e": {"value": aggregate_rate(ncoef, world, e2e_ms), "unit": "coeffs/s",
                     "h2d_bytes_per_step": ncoef * es, "d2h_bytes_per_step": ncoef * es, "ms_per_step": e2e_ms,
                     "steps": e2e_steps,
@@ -397,10 +425,34 @@ def run_ours(args):
                              "and copy-out of consecutive steps pipelined over two device buffer sets")},
             "gpu_launches": args.steps, "clocks": clocks, "accuracy": res}
     if not args.quick:
-        line["forms"] = secondary_forms(pg, workloads, dev, stream, G_h)
+        line["forms"] = secondary_forms(pg, workloads, dev, stream, G_h if N == 14 else None)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def profile_plan(pg, workloads, dev, stream, args):
+    """Warm-up + timed graph launches of the batched plan over the first B matrices of the
+    512-matrix uneven-N batch (for ncu on a reduced batch); prints the launch time."""
+    import torch
+
+    tdt = torch.complex128 if args.dtype == "c128" else torch.complex64
+    mats, Ns = workloads.batched_hermitian(workloads.SEEDS["batched"], batch=512)
+    mats, Ns = mats[:args.profile_batch], [int(n) for n in Ns[:args.profile_batch]]
+    rdt = torch.float64 if tdt == torch.complex128 else torch.float32
+    Gd = [torch.from_numpy(G).to(dev).to(tdt) for G in mats]
+    outs = [torch.empty(4 ** n, dtype=rdt if args.hermitian else tdt, device=dev) for n in Ns]
+    plan = pg.PauliPlan(Ns, dtype=tdt, hermitian=args.hermitian)
+    plan.bind(Gd, outs)
+    for _ in range(args.warmup):
+        plan.graph_launch()
+    torch.cuda.synchronize(dev)
+    ms = event_time(plan.graph_launch, args.steps, stream)
+    st = plan.status()
+    plan.close()
+    ncoef = sum(4 ** n for n in Ns)
+    print(json.dumps({"profile": True, "batch": len(Ns), "dtype": args.dtype, "hermitian": args.hermitian,
+                      "coefficients": ncoef, "ms_per_launch": ms, "status": st}), flush=True)
 
 
 def secondary_forms(pg, workloads, dev, stream, G14=None, only=None):
@@ -430,7 +482,36 @@ def secondary_forms(pg, workloads, dev, stream, G14=None, only=None):
         batched_forms(pg, workloads, dev, oracle, timed, forms)
     if want("adjoint"):
         adjoint_form(pg, workloads, dev, oracle, timed, forms)
+    if want("xhi") and G14 is not None:
+        xhi_form(pg, workloads, dev, oracle, timed, forms, G14)
     return forms
+
+
+def xhi_form(pg, workloads, dev, oracle, timed, forms, G14):
+    """x-class shards of the N=14 complex128 matrix on this one GPU: the block-XOR copy and the
+    shard decomposition (2^k blocks of N - k qubits + the in-place k-bit combine) for shard 1."""
+    import torch
+
+    from paper_2401_16378_gb300 import shard
+
+    N = 14
+    g = torch.from_numpy(G14).to(dev)
+    for k in (1, 3):
+        L = torch.empty((1 << N, 1 << (N - k)), dtype=torch.complex128, device=dev)
+        o = torch.empty(L.numel(), dtype=torch.complex128, device=dev)
+        ms_layout = timed(lambda: pg.xhi_layout(g, k, 1, out=L), 10)
+        ms = timed(lambda: pg.decompose_xhi(L, N, k, 1, out=o), 10)
+        j = np.random.default_rng(1400 + k).integers(0, o.numel(), 1024)
+        want = oracle.decompose_at(G14, shard.shard_indices(N, k, 1)[j])
+        err = float(np.max(np.abs(o.cpu().numpy()[j] - want)) / np.max(np.abs(G14)))
+        forms[f"n14_xhi_k{k}_c128"] = {
+            "shards": 1 << k, "shard_ms": ms, "layout_copy_ms": ms_layout,
+            "shard_coeffs_per_s": o.numel() / (ms * 1e-3),
+            "hbm_gbs_algorithmic": 2 * o.numel() * 16 / (ms * 1e-3) / 1e9,
+            "max_err_rel": err, "sample": "1024 seeded entries of shard 1 vs the oracle",
+            "note": "one shard on one GPU; 2^k such shards make the N=14 decomposition"}
+        del L, o
+    del g
 
 
 def n6_form(pg, workloads, dev, oracle, timed, forms):

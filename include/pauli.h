@@ -218,6 +218,33 @@ int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch
 int pauli_compose_batched(const void* const* c_list, const int* N_list, int batch, int dtype,
                           void* const* G_out_list, int scale_exp, void* stream);
 
+/* x-class shards. Every XY-mask x of Eq. (13) is an independent transform (Sec. 3 notes that the
+ * coefficients can be evaluated independently and distributed), so the 2^N classes can be split
+ * over 2^k devices by their top k bits x_hi. With m = N - k, the shard x_hi needs only the 2^k
+ * blocks of G (2^m x 2^m, at block row r_hi and block column r_hi ^ x_hi; r_hi = r >> m):
+ *   c(x, z) = 2^-k i^popc(x_hi & z_hi) sum_{r_hi} (-1)^popc(r_hi & z_hi) c_{B(r_hi)}(x_lo, z_lo),
+ * B(r_hi) the m-qubit block, x = (x_hi, x_lo), z = (z_hi, z_lo) split at bit m, and c_B(n_lo) the
+ * block's own coefficients, whose index n_lo = n(x_lo, z_lo) is the low 2m bits of n(x, z).
+ *
+ * Block-XOR layout L of the shard: D rows of 2^m elements, the blocks stacked by r_hi:
+ *   L[r * 2^m + j] = G[r, ((r_hi ^ x_hi) << m) | j],   0 <= r < D, 0 <= j < 2^m,
+ * 4^N / 2^k elements of dtype. pauli_xhi_layout builds it from a full device G (one 2D copy per
+ * block on the stream); a row-sharded G reaches it with one all-to-all, in which device w sends
+ * its block column w ^ g to device g.
+ *   G: device, D x D row-major; L: device, 4^N / 2^k elements; 0 <= k <= N - 1,
+ *   0 <= x_hi < 2^k; G and L must not overlap. */
+int pauli_xhi_layout(const void* G, int N, int k, int x_hi, int dtype, void* L, void* stream);
+
+/* The coefficients of the shard x_hi from its block-XOR layout L (above):
+ *   out[(z_hi << 2m) | n_lo] = c_n,  n = n_lo | (spread(x_hi ^ z_hi) | spread(z_hi) << 1) << 2m,
+ * for z_hi < 2^k and n_lo < 4^m (spread: bit t to bit 2t), 4^N / 2^k elements of dtype.
+ * One pauli_decompose of the 2^k blocks (m qubits, count 2^k, the given method; the same
+ * scratch) into out, then, in place, the k-bit Walsh-Hadamard transform over r_hi with the phase
+ * and the exact scale 2^-k, in passes of up to 4 bits (FP64 sums for both dtypes; complex64
+ * rounds once per pass). The shards' outputs together hold every c_n once; k = 0 is
+ * pauli_decompose. L and out must not overlap. */
+int pauli_decompose_xhi(const void* L, int N, int k, int x_hi, int dtype, void* out, int method, void* stream);
+
 /* Host-buffer round trip for callers whose data is in host memory: copies `count` matrices
  * from G_host (pinned memory gives asynchronous copies) to the caller's device buffer G_dev,
  * decomposes into out_dev, and copies the coefficients back to out_host, all on `stream`.
@@ -314,7 +341,7 @@ void pauli_plan_destroy(pauli_plan* plan);
  *                           calls on different streams get different library buffers.
  * PAULI_VARIANT_TILED16:    the same with two groups of 256 compute threads of 16 elements
  *                           each, working on alternate buffers.
- * PAULI_VARIANT_TWOSTAGE:   decomposition only, N 12..14 (the built-in choice at N = 13, 14): the
+ * PAULI_VARIANT_TWOSTAGE:   decomposition only, N 12..14 (the built-in choice there): the
  *                           same two stages, tiles and scratch ring, with every compute warp
  *                           running its 512 elements of a work item on its own (its own part of
  *                           the tile, its own copy of the stage-2 data, exchanges within the warp)

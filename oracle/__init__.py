@@ -36,7 +36,11 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile pauli_oracle.c into liboracle.so with gcc (OpenMP, no fast-math)."""
+    """Compile pauli_oracle.c into liboracle.so with gcc (OpenMP, no fast-math), and the
+    Gray-code CPU baseline (``oracle.gray``) beside it."""
+    from . import gray
+
+    gray.build(force)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",

@@ -16,3 +16,4 @@ from .api import (PauliDecompose, PauliDecomposeWeightedNorm, PauliError, PauliP
                   stream_status, version, weighted_norm, weighted_norm_autograd, weighted_norm_grad)
 from .api import (compose_batched, decompose_workspace_size, decompose_ws, pauli_decompose_workspace_size,  # noqa: F401
                   pauli_compose_batched, pauli_decompose_ws, release_workspaces, workspace_status)
+from .api import decompose_xhi, pauli_decompose_xhi, pauli_xhi_layout, xhi_layout  # noqa: F401

@@ -41,6 +41,8 @@ SIGNATURES = {
     "pauli_decompose_host": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp]),
     "pauli_decompose_host_stream": (_i, [_vpp, _vpp, _i, _i, _i, _vpp, _vpp, _i, _vp]),
     "pauli_compose_batched": (_i, [_vpp, _ip, _i, _i, _vpp, _i, _vp]),
+    "pauli_xhi_layout": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "pauli_decompose_xhi": (_i, [_vp, _i, _i, _i, _i, _vp, _i, _vp]),
     "pauli_decompose_batch_static": (_i, [_vpp, _ip, _i, _i, _vpp, _vp]),
     "pauli_plan_create": (_i, [_ip, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_void_p)]),
     "pauli_plan_create_hermitian": (_i, [_ip, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_void_p)]),

@@ -301,6 +301,41 @@ def pauli_decompose_list(Gs: Sequence[torch.Tensor], outs: Sequence[torch.Tensor
     return list(outs)
 
 
+def pauli_xhi_layout(G: torch.Tensor, k: int, x_hi: int, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """Block-XOR layout of the x-class shard x_hi of a (2^N, 2^N) CUDA matrix: a (2^N, 2^(N-k))
+    tensor, row r holding G[r, ((r >> (N-k)) ^ x_hi) << (N-k) | j] at column j."""
+    _device_tensor(G, "G")
+    N = _qubits_of_matrix(G)
+    if G.dim() != 2:
+        raise ValueError("G must be one (2^N, 2^N) matrix")
+    if out is None:
+        out = torch.empty((1 << N, 1 << (N - k)) if 0 <= k < N else (0,), dtype=G.dtype, device=G.device)
+    _device_tensor(out, "out")
+    if out.dtype != G.dtype or out.numel() != G.numel() >> k:
+        raise ValueError("out must match G in dtype and hold 4^N / 2^k elements")
+    check(_lib.load().pauli_xhi_layout(G.data_ptr(), N, int(k), int(x_hi), _dtype(G), out.data_ptr(),
+                                       _stream(stream)))
+    return out
+
+
+def pauli_decompose_xhi(L: torch.Tensor, N: int, k: int, x_hi: int, out: torch.Tensor | None = None,
+                        method="auto", stream=None) -> torch.Tensor:
+    """Coefficients of the x-class shard x_hi from its block-XOR layout L (4^N / 2^k elements):
+    out[(z_hi << 2(N-k)) | n_lo] = c_n for the n with top XY-mask bits x_hi (shard_indices)."""
+    _device_tensor(L, "L")
+    if out is None:
+        out = torch.empty(L.numel(), dtype=L.dtype, device=L.device)
+    _device_tensor(out, "out")
+    if out.dtype != L.dtype or out.numel() != L.numel():
+        raise ValueError("out must match L in dtype and number of elements")
+    if 0 <= k < N and L.numel() != (4 ** N) >> k:
+        raise ValueError("L must hold 4^N / 2^k elements")
+    check(_lib.load().pauli_decompose_xhi(L.data_ptr(), int(N), int(k), int(x_hi), _dtype(L), out.data_ptr(),
+                                          _method(method), _stream(stream)))
+    return out
+
+
 def pauli_compose_batched(cs: Sequence[torch.Tensor], outs: Sequence[torch.Tensor] | None = None, scale_exp: int = 0,
                           stream=None) -> list[torch.Tensor]:
     """G_b = 2^scale_exp sum_n c_b[n] P_n for coefficient vectors of different N, in one launch."""
@@ -530,6 +565,8 @@ compose = pauli_compose
 coeffs_at = pauli_coeffs_at
 decompose_list = pauli_decompose_list
 compose_batched = pauli_compose_batched
+xhi_layout = pauli_xhi_layout
+decompose_xhi = pauli_decompose_xhi
 decompose_ws = pauli_decompose_ws
 decompose_workspace_size = pauli_decompose_workspace_size
 decompose_host = pauli_decompose_host

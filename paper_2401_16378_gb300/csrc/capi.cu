@@ -510,6 +510,39 @@ int pauli_compose_batched(const void* const* c_list, const int* N_list, int batc
   return PAULI_OK;
 }
 
+int pauli_xhi_layout(const void* G, int N, int k, int x_hi, int dtype, void* L, void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (k < 0 || k >= N) return fail(PAULI_ERR_ARG, "k = %d outside [0, N - 1] for N = %d", k, N);
+  if (x_hi < 0 || x_hi >= (1 << k)) return fail(PAULI_ERR_ARG, "x_hi = %d outside [0, 2^k) for k = %d", x_hi, k);
+  if (!G) return fail(PAULI_ERR_NULL, "G is NULL");
+  if (!L) return fail(PAULI_ERR_NULL, "L is NULL");
+  const size_t es = elem_bytes(dtype);
+  if ((st = check_aligned(G, es, "G"))) return st;
+  if ((st = check_aligned(L, es, "L"))) return st;
+  const size_t full = ((size_t)1 << (2 * N)) * es;
+  if (overlaps(G, full, L, full >> k)) return fail(PAULI_ERR_ALIAS, "G and L overlap");
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+  cudaError_t e = pauli::xhi_layout(G, N, k, (uint32_t)x_hi, es, L, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_xhi_layout copies");
+  return PAULI_OK;
+}
+
+int pauli_decompose_xhi(const void* L, int N, int k, int x_hi, int dtype, void* out, int method, void* stream) {
+  int st;
+  if ((st = check_dtype(dtype))) return st;
+  if ((st = check_n(N))) return st;
+  if (k < 0 || k >= N) return fail(PAULI_ERR_ARG, "k = %d outside [0, N - 1] for N = %d", k, N);
+  if (x_hi < 0 || x_hi >= (1 << k)) return fail(PAULI_ERR_ARG, "x_hi = %d outside [0, 2^k) for k = %d", x_hi, k);
+  // the shard is 2^k stacked (N - k)-qubit blocks in, as many coefficients out
+  if ((st = check_pair(L, "L", N - k, 1ll << k, dtype, out, "out"))) return st;
+  if ((st = decompose_checked(L, N - k, 1ll << k, dtype, out, method, (cudaStream_t)stream))) return st;
+  cudaError_t e = pauli::launch_xhi_combine(out, N, k, (uint32_t)x_hi, dtype == PAULI_C64, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_xhi combine launch");
+  return PAULI_OK;
+}
+
 int pauli_decompose_batch_static(const void* const* G_list, const int* N_list, int batch, int dtype,
                                  void* const* out_list, void* stream) {
   int st;

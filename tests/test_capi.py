@@ -206,6 +206,29 @@ def test_workspace_entry_points_reject_bad_arguments(lib):
     assert lib.pauli_workspace_status(None, None) == NULL
 
 
+def test_xhi_entry_points_reject_bad_arguments(lib):
+    # N = 8, k = 2: G holds 4^8 = 65536 elements (1 MiB complex128), a shard 16384 (256 KiB)
+    assert lib.pauli_xhi_layout(P(A), 8, 2, 1, 7, P(B), None) == DTYPE
+    assert lib.pauli_xhi_layout(P(A), 8, 8, 0, C128, P(B), None) == ARG  # k = N
+    assert lib.pauli_xhi_layout(P(A), 8, -1, 0, C128, P(B), None) == ARG
+    assert lib.pauli_xhi_layout(P(A), 8, 2, 4, C128, P(B), None) == ARG  # x_hi = 2^k
+    assert b"x_hi" in lib.pauli_last_error()
+    assert lib.pauli_xhi_layout(None, 8, 2, 1, C128, P(B), None) == NULL
+    assert lib.pauli_xhi_layout(P(A + 8), 8, 2, 1, C128, P(B), None) == ALIGN
+    assert lib.pauli_xhi_layout(P(A), 8, 2, 1, C128, P(A + 0x80000), None) == ALIAS
+    assert lib.pauli_decompose_xhi(P(A), 8, 2, 1, 7, P(B), 0, None) == DTYPE
+    assert lib.pauli_decompose_xhi(P(A), 0, 0, 0, C128, P(B), 0, None) == ARG
+    assert lib.pauli_decompose_xhi(P(A), 8, 9, 0, C128, P(B), 0, None) == ARG
+    assert lib.pauli_decompose_xhi(P(A), 8, 2, -1, C128, P(B), 0, None) == ARG
+    assert lib.pauli_decompose_xhi(P(A), 8, 2, 1, C128, None, 0, None) == NULL
+    assert lib.pauli_decompose_xhi(P(A), 8, 2, 1, C128, P(A + 0x20000), 0, None) == ALIAS  # 256 KiB shard
+    assert lib.pauli_decompose_xhi(P(A), 8, 2, 1, C128, P(B), 9, None) == ARG  # method
+    lib.pauli_debug_fail_next_launches(2)
+    assert lib.pauli_decompose_xhi(P(A), 8, 2, 1, C128, P(B), 0, None) == CUDA
+    assert lib.pauli_xhi_layout(P(A), 8, 2, 1, C128, P(B), None) == CUDA
+    lib.pauli_debug_fail_next_launches(0)
+
+
 def test_injected_launch_failure_is_reported(lib):
     lib.pauli_debug_fail_next_launches(1)
     assert lib.pauli_decompose(P(A), 4, 1, C128, P(B), 0, None) == CUDA

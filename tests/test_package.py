@@ -50,3 +50,20 @@ def test_reference_arm_line_has_the_contract_keys():
     assert "workload" in d["config"]
     assert set(d["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"}
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_every_binding_is_exported_by_the_package():
+    """Each pauli_* binding in api.py, and its short alias, is reachable from the package."""
+    import inspect
+
+    import paper_2401_16378_gb300 as pg
+    from paper_2401_16378_gb300 import api
+
+    names = [n for n, f in inspect.getmembers(api, inspect.isfunction)
+             if n.startswith("pauli_") and f.__module__ == api.__name__]
+    assert "pauli_decompose_xhi" in names
+    for n in names:
+        assert hasattr(pg, n), n
+        short = n[len("pauli_"):]
+        if hasattr(api, short):
+            assert hasattr(pg, short), short
