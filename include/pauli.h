@@ -24,7 +24,13 @@
  *   - Every entry point returns a pauli_status; on failure pauli_last_error() returns a
  *     message for the calling thread. No C++ exception crosses this interface.
  *   - Non-finite input (Inf, NaN) yields NaN in every output that depends on it. Subnormal
- *     inputs of the XOR-diagonal path are read as zero.
+ *     inputs of the complex128 XOR-diagonal path are read as zero.
+ *   - Arithmetic. complex128: the XOR-diagonal path transforms exact int64 fixed-point values
+ *     at a per-XY-mask power-of-two scale; the plain path sums in FP64. complex64: compensated
+ *     FP32 -- the XOR-diagonal path splits every value error-free into a high part on a per-mask
+ *     power-of-two grid, whose sums are exact, and a low part that carries the rounding errors
+ *     (a mask whose values exceed about 2^(126 - N) in magnitude would leave the FP32 range and
+ *     gets NaN outputs); the plain path and the norms use TwoSum-compensated FP32 sums.
  */
 #ifndef PAULI_H
 #define PAULI_H
@@ -68,7 +74,7 @@ typedef enum {
  * contiguously at G into 4^N coefficients each, stored contiguously at out.
  *   out[k * 4^N + n] = c_n of matrix k = 2^-N Tr(P_n G_k)              Eq. (4), via Eq. (13).
  * dtype applies to both G and out. method: pauli_method.
- * With PAULI_XORDIAG at N = 13 and 14 the built-in launch shape is a two-stage one (see
+ * With PAULI_XORDIAG at N = 12..14 the built-in launch shape is a two-stage one (see
  * PAULI_VARIANT_TWOSTAGE below) that needs a scratch ring between its two stages. This entry point
  * takes it from a library-owned buffer per (device, stream), allocated with cudaMalloc at the
  * first tiled call on that pair, sized for every N so that it is never replaced, and kept until
@@ -214,7 +220,7 @@ int pauli_decompose_list(const void* const* G_list, const int* N_list, int batch
  * fixed order, so the call allocates nothing, keeps no state between calls, returns without
  * waiting for the GPU and can be captured in a CUDA graph. Same arithmetic as pauli_compose
  * (complex128: exact int64 transform of each XY-mask's values at a per-mask power-of-two scale;
- * complex64: TwoSum-compensated FP32). Input and output buffers must not overlap. */
+ * complex64: compensated FP32 on per-mask grids). Input and output buffers must not overlap. */
 int pauli_compose_batched(const void* const* c_list, const int* N_list, int batch, int dtype,
                           void* const* G_out_list, int scale_exp, void* stream);
 
@@ -228,8 +234,8 @@ int pauli_compose_batched(const void* const* c_list, const int* N_list, int batc
  *
  * Block-XOR layout L of the shard: D rows of 2^m elements, the blocks stacked by r_hi:
  *   L[r * 2^m + j] = G[r, ((r_hi ^ x_hi) << m) | j],   0 <= r < D, 0 <= j < 2^m,
- * 4^N / 2^k elements of dtype. pauli_xhi_layout builds it from a full device G (one 2D copy per
- * block on the stream); a row-sharded G reaches it with one all-to-all, in which device w sends
+ * 4^N / 2^k elements of dtype. pauli_xhi_layout builds it from a full device G (one copy kernel
+ * on the stream); a row-sharded G reaches it with one all-to-all, in which device w sends
  * its block column w ^ g to device g.
  *   G: device, D x D row-major; L: device, 4^N / 2^k elements; 0 <= k <= N - 1,
  *   0 <= x_hi < 2^k; G and L must not overlap. */
@@ -348,8 +354,8 @@ void pauli_plan_destroy(pauli_plan* plan);
  *                           and no barrier between the warps of an item. complex64 runs compensated
  *                           FP32: each value split into a high part on a per-mask power-of-two
  *                           grid, whose sums are exact, and a low part that carries the rounding
- *                           errors (error-free Fast2Sum against the grid's anchor); inputs above
- *                           2^(127 - N) in magnitude overflow. Scratch as for the tiled variants;
+ *                           errors (error-free Fast2Sum against the grid's anchor), re-split on
+ *                           the whole mask's grid between the stages. Scratch as for the tiled variants;
  *                           pauli_decompose_workspace_size reports it.
  * All variants compute bit-identical complex128 results, except that the two-stage ones re-scale
  * partial sums between the stages (an extra truncation below the class quantum, well inside

@@ -7,7 +7,7 @@
 
 namespace pauli {
 
-constexpr int kTiledSlots = 6;  // most scratch ring slots (the ring depth is chosen per N)
+constexpr int kTiledSlots = 16;  // most scratch ring slots (the ring depth is chosen per N)
 
 // Device control block at the start of the workspace. Everything from `counter` on is
 // cleared before every launch; `status` keeps the first error until pauli_stream_status reads
@@ -22,7 +22,7 @@ struct TiledCtrl {
   int pad1[6];
   uint32_t emax[kTiledSlots][64];  // per class of the slot's block: (generation + 1) << 11 | exponent
 };
-constexpr size_t kTiledCtrlBytes = 2048;  // control block, padded; the slots follow
+constexpr size_t kTiledCtrlBytes = 8192;  // control block, padded; the slots follow
 static_assert(sizeof(TiledCtrl) <= kTiledCtrlBytes, "control block fits its padding");
 
 bool tiled_supported(int N);

@@ -91,11 +91,12 @@ struct Geo {
   static constexpr size_t kSlotE = (size_t)NR * 64 * 4;
   static constexpr size_t kEOct = (size_t)NR * 8 * 4;
   static constexpr size_t kBuf = kChunk + kEOct + 128;
-  // ring depth: enough blocks in flight for the items the CTAs hold (measured: 6 x 8 MiB at N = 13,
-  // 4 x 16 MiB at N = 14)
-  static constexpr int NS = N <= 12 ? 6 : N == 13 ? 6 : 4;
+  // ring depth and lag, measured: 13 x 4 MiB with a lag of 6 blocks at N = 12 (0.163 ms against
+  // 0.180 ms with 6 slots and a lag of 3), 6 x 8 MiB / 3 at N = 13, 4 x 16 MiB / 2 at N = 14 (deeper
+  // rings spill from L2 there and are slower)
+  static constexpr int NS = N <= 12 ? 13 : N == 13 ? 6 : 4;
   // stage-2 items of block b follow stage-1 tiles of block b + LAG in the work order
-  static constexpr int LAG = N <= 12 ? 3 : N == 13 ? 3 : 2;
+  static constexpr int LAG = N <= 12 ? 6 : N == 13 ? 3 : 2;
   static_assert(NS <= kTiledSlots, "control block has room for the ring");
   static_assert(NS >= LAG + 2, "slot reuse waits on items taken at least a group earlier");
   static constexpr size_t kPBase = kTiledCtrlBytes;

@@ -133,17 +133,51 @@ cudaError_t launch_xhi_combine(void* out, int N, int k, uint32_t x_hi, bool c64,
   return cudaSuccess;
 }
 
+namespace {
+
+// L[r][j] = G[r][((r_hi ^ x_hi) << m) | j], moved in words of W bytes: word w of row r of L
+// (rows of M elements = rw words) comes from the same word of the row's block in G.
+template <class W>
+__global__ void __launch_bounds__(256) xhi_layout_kernel(const char* __restrict__ G, char* __restrict__ L, int N,
+                                                         int m, uint32_t x_hi, size_t elem, int rw_log,
+                                                         unsigned long long words) {
+  const unsigned long long row_bytes = (unsigned long long)elem << N;
+  const unsigned long long rw_mask = (1ull << rw_log) - 1ull;  // rows of L hold 2^rw_log words
+  for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < words;
+       w += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = w >> rw_log, c = w & rw_mask;
+    const unsigned long long cb = ((r >> m) ^ x_hi) << m;  // first column of the row's block
+    const W v = __ldcs(reinterpret_cast<const W*>(G + r * row_bytes + cb * elem) + c);
+    __stcs(reinterpret_cast<W*>(L) + w, v);
+  }
+}
+
+}  // namespace
+
 cudaError_t xhi_layout(const void* G, int N, int k, uint32_t x_hi, size_t elem, void* L, cudaStream_t s) {
   const int m = N - k;
-  const size_t M = (size_t)1 << m, D = (size_t)1 << N;
-  for (size_t rh = 0; rh < ((size_t)1 << k); ++rh) {
-    const size_t ch = rh ^ x_hi;
-    const char* src = static_cast<const char*>(G) + (rh * M * D + ch * M) * elem;
-    char* dst = static_cast<char*>(L) + rh * M * M * elem;
-    cudaError_t e = cudaMemcpy2DAsync(dst, M * elem, src, D * elem, M * elem, M, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const unsigned long long bytes = (unsigned long long)elem << (2 * N - k);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // 16-byte words when both buffers allow them (a row of L is at least 16 bytes: m >= 1)
+  const bool wide = !((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(L)) & 15u);
+  const unsigned long long words = bytes / (wide ? 16u : elem);
+  const unsigned long long want = (words + 255) / 256, cap = (unsigned long long)sms * 8ull;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  const char* g = static_cast<const char*>(G);
+  char* l = static_cast<char*>(L);
+  const int elog = elem == 16 ? 4 : 3;
+  // words per row of L: 2^m elements of 2^elog bytes in words of 16 bytes or of one element
+  const int rw_log = m + elog - (wide ? 4 : elog);
+  if (wide)
+    xhi_layout_kernel<uint4><<<grid, 256, 0, s>>>(g, l, N, m, x_hi, elem, rw_log, words);
+  else if (elem == 16)
+    xhi_layout_kernel<double2><<<grid, 256, 0, s>>>(g, l, N, m, x_hi, elem, rw_log, words);
+  else
+    xhi_layout_kernel<float2><<<grid, 256, 0, s>>>(g, l, N, m, x_hi, elem, rw_log, words);
+  return cudaGetLastError();
 }
 
 }  // namespace pauli

@@ -284,8 +284,19 @@ struct ArC128 {
   }
 };
 
+// complex64, compensated FP32 on a per-mask power-of-two grid. Each real value is an
+// unevaluated sum hi + lo of two floats, split error-free on input: with the anchor
+// C = 1.5 * 2^23 * q, hi = fl(x + C) - C rounds x to the grid q and lo = x - hi is exact (Fast2Sum
+// with |C| > |x|; the ExtractScalar step of Rump, Ogita and Oishi, SIAM J. Sci. Comput. 31(1),
+// 2008). q = 2^(N + 1 - 23) 2^(E - 127) for the mask's largest float exponent field E, so every sum
+// of 2^N high parts stays below 2^24 q: all high-part additions are exact (their TwoSum error term
+// is identically zero and is not computed), and the low parts, added in plain FP32, carry the
+// compensation. Error before the final rounding: about N 2^(N - 47) 2^(E - 127) per coefficient.
+// A mask whose anchor would leave the FP32 range (inputs above about 2^(126 - N)) or that holds
+// a non-finite value gets a NaN anchor, so all its outputs are NaN.
 struct C64Conv {
-  float scale;
+  float anchor;  // 1.5 * 2^23 * grid
+  float scale;   // output scale 2^out_scale, exact
 };
 
 struct ArC64 {
@@ -294,6 +305,96 @@ struct ArC64 {
     float rh, rl, ih, il;
   };
   using Conv = C64Conv;
+  static constexpr bool kScaled = true;
+  __device__ static __forceinline__ Raw load(const void* p, unsigned long long i) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::128B.v2.f32 {%0,%1}, [%2];"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(reinterpret_cast<const float2*>(p) + i));
+    return v;
+  }
+  __device__ static __forceinline__ void prefetch(const void* p, unsigned long long i) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const float2*>(p) + i));
+  }
+  // largest exponent field of the two parts (compares as an integer)
+  __device__ static __forceinline__ uint32_t exp_key(const Raw& r) {
+    return max(__float_as_uint(r.x) & 0x7F800000u, __float_as_uint(r.y) & 0x7F800000u);
+  }
+  __device__ static __forceinline__ uint4 raw_pack(const Raw& r) { return make_uint4(__float_as_uint(r.x), __float_as_uint(r.y), 0u, 0u); }
+  __device__ static __forceinline__ Raw raw_unpack(const uint4& q) { return make_float2(__uint_as_float(q.x), __uint_as_float(q.y)); }
+  // anchor for a growth of 2^G over a mask whose largest exponent field is E: exponent field
+  // E + G, significand 1.5; NaN when that leaves the finite range or E marks Inf / NaN
+  __device__ static __forceinline__ float anchor(uint32_t E, int G) {
+    const uint32_t e = E + (uint32_t)G;
+    return __uint_as_float(E >= 0xFFu || e > 0xFEu ? 0x7FC00000u : (e << 23) | 0x00400000u);
+  }
+  __device__ static __forceinline__ Conv make_conv(int N, uint32_t Ekey, int out_scale_exp) {
+    return Conv{anchor(Ekey >> 23, N + 1), __int_as_float((127 + out_scale_exp) << 23)};
+  }
+  __device__ static __forceinline__ void split(float x, float C, float& hi, float& lo) {
+    hi = __fsub_rn(__fadd_rn(x, C), C);
+    lo = __fsub_rn(x, hi);
+  }
+  // Converted element times i^k (k mod 4; exact).
+  template <int LPRE>
+  __device__ static __forceinline__ Elem convert(const Raw& r, const Conv& cv, uint32_t k) {
+    float re = r.x, im = r.y;
+    mul_i_pow(re, im, k);
+    Elem e;
+    split(re, cv.anchor, e.rh, e.rl);
+    split(im, cv.anchor, e.ih, e.il);
+    return e;
+  }
+  __device__ static __forceinline__ void bfly(Elem& a, Elem& b) {
+    const float rh0 = __fadd_rn(a.rh, b.rh), rh1 = __fsub_rn(a.rh, b.rh);
+    const float rl0 = __fadd_rn(a.rl, b.rl), rl1 = __fsub_rn(a.rl, b.rl);
+    const float ih0 = __fadd_rn(a.ih, b.ih), ih1 = __fsub_rn(a.ih, b.ih);
+    const float il0 = __fadd_rn(a.il, b.il), il1 = __fsub_rn(a.il, b.il);
+    a = Elem{rh0, rl0, ih0, il0};
+    b = Elem{rh1, rl1, ih1, il1};
+  }
+  __device__ static __forceinline__ uint4 pack(const Elem& a) {
+    return make_uint4(__float_as_uint(a.rh), __float_as_uint(a.rl), __float_as_uint(a.ih), __float_as_uint(a.il));
+  }
+  __device__ static __forceinline__ Elem unpack(const uint4& q) {
+    return Elem{__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), __uint_as_float(q.w)};
+  }
+  __device__ static __forceinline__ float2 out_value(const Elem& a, const Conv& cv, uint32_t k) {
+    float re = __fadd_rn(a.rh, a.rl), im = __fadd_rn(a.ih, a.il);
+    mul_i_pow(re, im, k);
+    return make_float2(__fmul_rn(re, cv.scale), __fmul_rn(im, cv.scale));
+  }
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    reinterpret_cast<float2*>(p)[i] = out_value(a, cv, k);
+  }
+  __device__ static __forceinline__ void store_value(void* p, unsigned long long i, const float2& o) {
+    reinterpret_cast<float2*>(p)[i] = o;
+  }
+  __device__ static __forceinline__ Raw weigh(const Raw& r, float f) { return make_float2(r.x * f, r.y * f); }
+  __device__ static __forceinline__ Raw conj(const Raw& r) { return make_float2(r.x, -r.y); }
+  __device__ static __forceinline__ Raw real_part(const Raw& r) { return make_float2(r.x, 0.f); }
+  __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
+                                                    uint32_t k, uint64_t pol) {
+    const float2 o = out_value(a, cv, k);
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1,%2}, %3;" ::"l"(reinterpret_cast<float2*>(p) + i),
+                 "f"(o.x), "f"(o.y), "l"(pol)
+                 : "memory");
+  }
+  __device__ static __forceinline__ void align(Elem&, int) {}
+};
+
+// complex64 with TwoSum-compensated butterflies (FP32 value + FP32 error term per part): the
+// arithmetic of the block-tiled two-stage kernel, whose tiles have no common grid.
+struct C64TConv {
+  float scale;
+};
+
+struct ArC64T {
+  using Raw = float2;
+  struct Elem {
+    float rh, rl, ih, il;
+  };
+  using Conv = C64TConv;
   static constexpr bool kScaled = false;
   __device__ static __forceinline__ Raw load(const void* p, unsigned long long i) {
     float2 v;
@@ -383,6 +484,23 @@ struct ReOut<ArC128> : ArC128 {
 
 template <>
 struct ReOut<ArC64> : ArC64 {
+  __device__ static __forceinline__ float re_value(const Elem& a, const Conv& cv, uint32_t k) {
+    const float v = (k & 1u) ? __fadd_rn(a.ih, a.il) : __fadd_rn(a.rh, a.rl);
+    return __fmul_rn(((k ^ (k >> 1)) & 1u) ? -v : v, cv.scale);
+  }
+  __device__ static __forceinline__ void store(void* p, unsigned long long i, const Elem& a, const Conv& cv, uint32_t k) {
+    reinterpret_cast<float*>(p)[i] = re_value(a, cv, k);
+  }
+  __device__ static __forceinline__ void store_hint(void* p, unsigned long long i, const Elem& a, const Conv& cv,
+                                                    uint32_t k, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(reinterpret_cast<float*>(p) + i),
+                 "f"(re_value(a, cv, k)), "l"(pol)
+                 : "memory");
+  }
+};
+
+template <>
+struct ReOut<ArC64T> : ArC64T {
   __device__ static __forceinline__ float re_value(const Elem& a, const Conv& cv, uint32_t k) {
     const float v = (k & 1u) ? __fadd_rn(a.ih, a.il) : __fadd_rn(a.rh, a.rl);
     return __fmul_rn(((k ^ (k >> 1)) & 1u) ? -v : v, cv.scale);

@@ -85,3 +85,21 @@ def test_plain_method_and_layout_copy():
     want = oracle.decompose_full(G_h)
     got = shard.assemble(_shards(G, N, k, method="plain"), N, k)
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(G_h))
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_layout_copy_of_unaligned_views(dtype):
+    """Buffers at an odd element offset (8-byte aligned complex64) take the element-wise copy."""
+    N, k = 6, 3
+    D, M = 1 << N, 1 << (N - k)
+    G_h = workloads.gaussian_complex(N, 72, NP[dtype])
+    gbuf = torch.zeros(D * D + 1, dtype=dtype, device="cuda")
+    gbuf[1:] = torch.from_numpy(G_h.reshape(-1)).cuda()
+    G = gbuf[1:].view(D, D)
+    lbuf = torch.zeros(D * M + 1, dtype=dtype, device="cuda")
+    for g in range(1 << k):
+        pg.xhi_layout(G, k, g, out=lbuf[1:].view(D, M))
+        L = lbuf[1:].view(D, M).cpu().numpy()
+        for r in range(D):
+            cb = (r >> (N - k)) ^ g
+            assert np.array_equal(L[r], G_h[r, cb * M:(cb + 1) * M])
