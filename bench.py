@@ -371,7 +371,7 @@ def run_ours(args):
     G_pin = torch.from_numpy(G_h).pin_memory()
     out_pins = [torch.empty(ncoef, dtype=torch.complex128).pin_memory() for _ in range(2)]
     G_devs, out_devs = [G.view(-1), torch.empty_like(G).view(-1)], [out, torch.empty_like(out)]
-    e2e_steps = max(4, min(args.steps, 16))  # enough steps to amortise the pipeline fill and drain
+    e2e_steps = max(4, min(args.steps, 32))  # enough steps to amortise the pipeline fill and drain
 
     def e2e_run(k):
         pg.pauli_decompose_host_stream([G_pin] * k, [out_pins[i % 2] for i in range(k)], G_devs, out_devs,
@@ -523,7 +523,23 @@ def n6_form(pg, workloads, dev, oracle, timed, forms):
     o6 = torch.empty(4 ** 6, dtype=torch.complex128, device=dev)
     ms6 = timed(lambda: pg.decompose(g6, out=o6, method="plain"), 50)
     err6 = float(np.max(np.abs(o6.cpu().numpy() - oracle.decompose_full(G6))) / np.max(np.abs(G6)))
-    forms["n6_plain_c128"] = {"us_per_call": ms6 * 1e3, "coeffs_per_s": 4 ** 6 / (ms6 * 1e-3), "max_err_rel": err6}
+    # the same 50 calls captured in one CUDA graph: the kernel's own latency, without the
+    # Python-side cost of each call
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        pg.decompose(g6, out=o6, method="plain")
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(50):
+            pg.decompose(g6, out=o6, method="plain")
+    ms6g = timed(graph.replay, 5) / 50
+    forms["n6_plain_c128"] = {"us_per_call": ms6 * 1e3, "coeffs_per_s": 4 ** 6 / (ms6 * 1e-3), "max_err_rel": err6,
+                              "graph_us_per_call": ms6g * 1e3,
+                              "graph_coeffs_per_s": 4 ** 6 / (ms6g * 1e-3),
+                              "note": "us_per_call: separate calls from Python; graph_: 50 calls in one CUDA graph"}
+    del graph
     # the complex64 path on the same input (TwoSum-compensated FP32), error against the FP64 oracle
     # of the exactly upcast input
     G6s = G6.astype(np.complex64)

@@ -71,9 +71,12 @@ struct AccC64 {
 // bit h of r set (h the top set bit of x), is read as conj(G[r ^ x, r]).
 // REALIN (complex128 arithmetic, with RE): G is a real float64 matrix; the output is the real
 // a_n with c_n = i^(k mod 2) a_n, k = popc(x & z) the number of Y factors.
+// WS > 1 (small grids): the WS warps of a block share one tile and take consecutive runs of
+// its Gray steps; their partial sums meet in shared memory, added in warp order.
 template <bool C64, bool RE, bool UPPER = false, bool REALIN = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(const void* __restrict__ Gv, int N,
-                                                                             long long count, void* __restrict__ outv) {
+                                                                             long long count, void* __restrict__ outv,
+                                                                             int WS) {
   using Acc = typename std::conditional<C64, AccC64, AccC128>::type;
   const uint32_t D = 1u << N;
   const int lcw = N < 3 ? N : 3;  // log2 CW
@@ -88,8 +91,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
 
   const unsigned long long tiles_x = D >> lcw, tiles_z = D >> lkz;
   const unsigned long long tiles_per_mat = tiles_x * tiles_z;
-  const unsigned long long w = (unsigned long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (w >= tiles_per_mat * (unsigned long long)count) return;  // whole warp leaves together
+  const uint32_t wchunk = WS > 1 ? threadIdx.x >> 5 : 0u;  // this warp's run of Gray steps
+  const unsigned long long w =
+      WS > 1 ? (unsigned long long)blockIdx.x : (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= tiles_per_mat * (unsigned long long)count) return;  // whole warp (whole block for WS > 1) leaves together
   const unsigned long long kmat = w / tiles_per_mat;
   const unsigned long long tile = w % tiles_per_mat;
   const uint32_t x = (uint32_t)(tile / tiles_z) * CW + c;
@@ -99,23 +104,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
   Acc acc;
   acc.zero();
   if (active) {
-    // initial signs for g = 0 (row r = rsub)
+    const uint32_t steps_all = D >> lrs;
+    const uint32_t steps = steps_all / (uint32_t)WS, gbeg = wchunk * steps;  // WS divides steps_all
+    // initial signs at the first Gray step of the run (row r = rsub | gray(gbeg) << lrs)
+    const uint32_t r0 = rsub | ((gbeg ^ (gbeg >> 1)) << lrs);
     uint32_t signs = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      if ((uint32_t)k < KZ) signs |= (uint32_t)(__popc(rsub & (zb + k)) & 1) << k;
+      if ((uint32_t)k < KZ) signs |= (uint32_t)(__popc(r0 & (zb + k)) & 1) << k;
     const uint32_t kmask = (1u << KZ) - 1u;
-    const uint32_t steps = D >> lrs;
-    if (C64) {
-      const float2* G = reinterpret_cast<const float2*>(Gv) + kmat * (unsigned long long)D * D;
-      for (uint32_t g = 0; g < steps; ++g) {
-        if (g) {
-          const int zbit = __ffs(g) - 1 + lrs;  // row bit changed by this Gray step
-          const uint32_t flip = zbit < lkz ? k_pattern(zbit) : (((zb >> zbit) & 1u) ? 0xFFu : 0u);
-          signs ^= flip & kmask;
-        }
-        const uint32_t r = rsub | ((g ^ (g >> 1)) << lrs);
-        float2 e;
+    using Val = typename std::conditional<C64, float2, double2>::type;
+    const unsigned long long mbase = kmat * (unsigned long long)D * D;
+    // element of row r of the XOR-diagonal of x (mirrored / real input as the flags say)
+    auto load = [&](uint32_t r) -> Val {
+      if constexpr (REALIN) {
+        return Val{__ldg(&reinterpret_cast<const double*>(Gv)[mbase + (unsigned long long)r * D + (r ^ x)]), 0.0};
+      } else {
+        const Val* G = reinterpret_cast<const Val*>(Gv) + mbase;
+        Val e;
         if (UPPER && hx < 32u && ((r >> hx) & 1u)) {
           e = __ldg(&G[(unsigned long long)(r ^ x) * D + r]);
           e.y = -e.y;
@@ -123,34 +129,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
           e = __ldg(&G[(unsigned long long)r * D + (r ^ x)]);
           if (UPPER && x == 0u) e.y = 0;  // the diagonal: its imaginary parts are not used
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if ((uint32_t)k < KZ) acc.add(k, e.x, e.y, (signs >> k) & 1u);
+        return e;
       }
-    } else {
-      const double2* G = reinterpret_cast<const double2*>(Gv) + kmat * (unsigned long long)D * D;
-      for (uint32_t g = 0; g < steps; ++g) {
-        if (g) {
-          const int zbit = __ffs(g) - 1 + lrs;
+    };
+    // The loads of kBatch consecutive Gray steps are independent: issue them together, then
+    // accumulate in step order (the sign recurrence and the sums keep their sequence).
+    constexpr uint32_t kBatch = 4;
+    for (uint32_t g0 = gbeg; g0 < gbeg + steps; g0 += kBatch) {
+      Val e[kBatch];
+#pragma unroll
+      for (uint32_t u = 0; u < kBatch; ++u) {
+        const uint32_t g = g0 + u;
+        if (g < gbeg + steps) e[u] = load(rsub | ((g ^ (g >> 1)) << lrs));
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kBatch; ++u) {
+        const uint32_t g = g0 + u;
+        if (g >= gbeg + steps) break;
+        if (g != gbeg) {
+          const int zbit = __ffs(g) - 1 + lrs;  // row bit changed by this Gray step
           const uint32_t flip = zbit < lkz ? k_pattern(zbit) : (((zb >> zbit) & 1u) ? 0xFFu : 0u);
           signs ^= flip & kmask;
         }
-        const uint32_t r = rsub | ((g ^ (g >> 1)) << lrs);
-        double2 e;
-        if (REALIN) {
-          e = make_double2(__ldg(&reinterpret_cast<const double*>(Gv)[kmat * (unsigned long long)D * D +
-                                                                       (unsigned long long)r * D + (r ^ x)]),
-                           0.0);
-        } else if (UPPER && hx < 32u && ((r >> hx) & 1u)) {
-          e = __ldg(&G[(unsigned long long)(r ^ x) * D + r]);
-          e.y = -e.y;
-        } else {
-          e = __ldg(&G[(unsigned long long)r * D + (r ^ x)]);
-          if (UPPER && x == 0u) e.y = 0;  // the diagonal: its imaginary parts are not used
-        }
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-          if ((uint32_t)k < KZ) acc.add(k, e.x, e.y, (signs >> k) & 1u);
+          if ((uint32_t)k < KZ) acc.add(k, e[u].x, e[u].y, (signs >> k) & 1u);
       }
     }
   }
@@ -166,6 +169,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) plain_decompose_kernel(co
     for (int k = 0; k < 8; ++k) {
       tr[k] += __shfl_xor_sync(0xFFFFFFFFu, tr[k], m);
       ti[k] += __shfl_xor_sync(0xFFFFFFFFu, ti[k], m);
+    }
+  }
+  if (WS > 1) {  // the block's warps meet: partials of the first row subset's lanes, [warp][c][k]
+    __shared__ double part[4][8][8][2];
+    if (rsub == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        part[wchunk][c][k][0] = tr[k];
+        part[wchunk][c][k][1] = ti[k];
+      }
+    }
+    __syncthreads();
+    if (wchunk != 0) return;
+    if (rsub == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        tr[k] = part[0][c][k][0];
+        ti[k] = part[0][c][k][1];
+        for (int q = 1; q < WS; ++q) {
+          tr[k] += part[q][c][k][0];
+          ti[k] += part[q][c][k][1];
+        }
+      }
     }
   }
   if (rsub != 0) return;
@@ -315,26 +341,44 @@ __global__ void __launch_bounds__(256) plain_compose_kernel(const void* __restri
 
 }  // namespace
 
+// Warps per block of the plain kernels: one for small grids, so that the blocks (and their FP64
+// work) spread over the SMs -- at N = 6 the 64 warps of a matrix would otherwise share 8 SMs'
+// FP64 pipes -- and kWarpsPerBlock otherwise.
+static int plain_warps_per_block(unsigned long long tiles) { return tiles < 4096ull ? 1 : kWarpsPerBlock; }
+// Warps sharing one tile: up to 4 for small grids (one per SM sub-partition and its FP64 unit),
+// dividing the Gray steps of each lane (2^N / row subsets).
+static int plain_warps_per_tile(int N, unsigned long long tiles) {
+  const int lcw = N < 3 ? N : 3;
+  const int lrs = (5 - lcw) < N ? (5 - lcw) : N;
+  const unsigned long long steps = (1ull << N) >> lrs;
+  if (tiles >= 4096ull) return 1;
+  return steps >= 4 ? 4 : (int)steps;
+}
+
 cudaError_t launch_plain_decompose(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s,
                                    bool re, bool upper) {
   const int lcw = N < 3 ? N : 3, lkz = lcw;
   const unsigned long long tiles = ((1ull << N) >> lcw) * ((1ull << N) >> lkz) * (unsigned long long)count;
-  const unsigned long long blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int ws = plain_warps_per_tile(N, tiles);
+  const int wpb = ws > 1 ? ws : plain_warps_per_block(tiles);
+  const unsigned long long blocks = ws > 1 ? tiles : (tiles + wpb - 1) / wpb;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
   auto kern = c64 ? (re ? (upper ? plain_decompose_kernel<true, true, true> : plain_decompose_kernel<true, true>)
                         : plain_decompose_kernel<true, false>)
                   : (re ? (upper ? plain_decompose_kernel<false, true, true> : plain_decompose_kernel<false, true>)
                         : plain_decompose_kernel<false, false>);
-  kern<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
+  kern<<<(unsigned)blocks, wpb * 32, 0, s>>>(G, N, count, out, ws);
   return cudaGetLastError();
 }
 
 cudaError_t launch_plain_decompose_real(const void* G, int N, long long count, void* out, cudaStream_t s) {
   const int lcw = N < 3 ? N : 3, lkz = lcw;
   const unsigned long long tiles = ((1ull << N) >> lcw) * ((1ull << N) >> lkz) * (unsigned long long)count;
-  const unsigned long long blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int ws = plain_warps_per_tile(N, tiles);
+  const int wpb = ws > 1 ? ws : plain_warps_per_block(tiles);
+  const unsigned long long blocks = ws > 1 ? tiles : (tiles + wpb - 1) / wpb;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-  plain_decompose_kernel<false, true, false, true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(G, N, count, out);
+  plain_decompose_kernel<false, true, false, true><<<(unsigned)blocks, wpb * 32, 0, s>>>(G, N, count, out, ws);
   return cudaGetLastError();
 }
 
