@@ -260,3 +260,37 @@ def test_two_stage_variants_agree_bit_for_bit_in_complex128(N):
     outs = [run_tiled(Gd, N, torch.complex128, v) for v in TILED]
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+def _class_of_all(N):
+    n_all = np.arange(4 ** N, dtype=np.int64)
+    even = np.zeros_like(n_all)
+    odd = np.zeros_like(n_all)
+    for t in range(N):
+        even |= ((n_all >> (2 * t)) & 1) << t
+        odd |= ((n_all >> (2 * t + 1)) & 1) << t
+    return even ^ odd
+
+
+@pytest.mark.parametrize("N,variant", [(12, "twostage"), (10, None)])
+@pytest.mark.parametrize("bad", [1e36, np.inf])
+def test_complex64_out_of_range_entry_gives_nan_for_its_mask_only(N, variant, bad):
+    """A complex64 value beyond the compensated grid's range (above about 2^(126 - N)) or a
+    non-finite one makes every coefficient of its XY-mask NaN and leaves the others exact."""
+    D = 1 << N
+    G = workloads.gaussian_complex(N, 2600 + N).astype(np.complex64)
+    r, q = 700 % D, 3001 % D
+    G[r, q] = np.complex64(bad)
+    Gd = dev(G)
+    if variant:
+        got = run_tiled(Gd, N, torch.complex64, variant)
+    else:
+        got = host(pg.decompose(Gd, method="xordiag"))
+    mask = _class_of_all(N) == (r ^ q)
+    assert np.all(np.isnan(got[mask]))
+    assert not np.any(np.isnan(got[~mask]))
+    idx = workloads.sample_indices(N, 2601, k=512)
+    idx = idx[~mask[idx.astype(np.int64)]]
+    Gc = G.astype(np.complex128)
+    Gc[r, q] = 0  # the other masks never read the entry
+    assert_close(got[idx.astype(np.int64)], oracle.decompose_at(Gc, idx), np.max(np.abs(Gc)), torch.complex64)
