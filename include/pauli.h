@@ -244,11 +244,14 @@ int pauli_xhi_layout(const void* G, int N, int k, int x_hi, int dtype, void* L, 
 /* The coefficients of the shard x_hi from its block-XOR layout L (above):
  *   out[(z_hi << 2m) | n_lo] = c_n,  n = n_lo | (spread(x_hi ^ z_hi) | spread(z_hi) << 1) << 2m,
  * for z_hi < 2^k and n_lo < 4^m (spread: bit t to bit 2t), 4^N / 2^k elements of dtype.
- * One pauli_decompose of the 2^k blocks (m qubits, count 2^k, the given method; the same
- * scratch) into out, then, in place, the k-bit Walsh-Hadamard transform over r_hi with the phase
- * and the exact scale 2^-k, in passes of up to 4 bits (FP64 sums for both dtypes; complex64
- * rounds once per pass). The shards' outputs together hold every c_n once; k = 0 is
- * pauli_decompose. L and out must not overlap. */
+ * For N = 12..14 with m >= 6 and PAULI_AUTO / PAULI_XORDIAG (L 16-byte aligned): one launch
+ * of the two-stage kernel over the shard's classes, reading L's tiles and writing the compact
+ * order directly, bit for bit the values pauli_decompose gives for those coefficients with its
+ * two-stage shape (the scratch of pauli_decompose). Otherwise: one pauli_decompose of the 2^k
+ * blocks (m qubits, count 2^k, the given method) into out, then, in place, the k-bit
+ * Walsh-Hadamard transform over r_hi with the phase and the exact scale 2^-k, in passes of up
+ * to 4 bits (FP64 sums for both dtypes; complex64 rounds once per pass). The shards' outputs
+ * together hold every c_n once; k = 0 is pauli_decompose. L and out must not overlap. */
 int pauli_decompose_xhi(const void* L, int N, int k, int x_hi, int dtype, void* out, int method, void* stream);
 
 /* Host-buffer round trip for callers whose data is in host memory: copies `count` matrices

@@ -537,6 +537,15 @@ int pauli_decompose_xhi(const void* L, int N, int k, int x_hi, int dtype, void* 
   if (x_hi < 0 || x_hi >= (1 << k)) return fail(PAULI_ERR_ARG, "x_hi = %d outside [0, 2^k) for k = %d", x_hi, k);
   // the shard is 2^k stacked (N - k)-qubit blocks in, as many coefficients out
   if ((st = check_pair(L, "L", N - k, 1ll << k, dtype, out, "out"))) return st;
+  int m = 0;
+  if ((st = resolve_method(method, N - k, &m))) return st;
+  if (m == PAULI_XORDIAG && N >= 12 && N <= 14 && N - k >= 6 && !((uintptr_t)L & 15u)) {
+    // the whole shard in one two-stage launch
+    if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+    cudaError_t e = pauli::twostage_launch_xhi(L, N, k, (uint32_t)x_hi, dtype == PAULI_C64, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_xhi launch");
+    return PAULI_OK;
+  }
   if ((st = decompose_checked(L, N - k, 1ll << k, dtype, out, method, (cudaStream_t)stream))) return st;
   cudaError_t e = pauli::launch_xhi_combine(out, N, k, (uint32_t)x_hi, dtype == PAULI_C64, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_xhi combine launch");

@@ -58,6 +58,9 @@ cudaError_t launch_compose_batched(const void* const* c_list, const int* N_list,
 // x-class shards (xhi.cu): the in-place combine of 2^k stacked (N - k)-qubit decompositions
 // into the coefficients with top XY-mask bits x_hi, and the block-XOR copy of G that feeds it.
 cudaError_t launch_xhi_combine(void* out, int N, int k, uint32_t x_hi, bool c64, cudaStream_t s);
+// The shard in one two-stage launch from its layout (N 12..14, N - k >= 6, L 16-byte aligned):
+// cudaErrorNotSupported otherwise (twostage_*.cu).
+cudaError_t twostage_launch_xhi(const void* L, int N, int k, uint32_t x_hi, bool c64, void* out, cudaStream_t s);
 cudaError_t xhi_layout(const void* G, int N, int k, uint32_t x_hi, size_t elem, void* L, cudaStream_t s);
 // Adds n partial losses (fixed order) into *loss (norm.cu).
 cudaError_t launch_norm_final(const double* partial, long long n, bool c64, void* loss, cudaStream_t s);

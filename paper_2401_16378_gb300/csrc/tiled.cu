@@ -70,6 +70,22 @@ cudaError_t tiled_tensor_map(CUtensorMap* map, const void* G, int N, int count, 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t tiled_tensor_map_rows(CUtensorMap* map, const void* G, int wlog, long long rows, int elem) {
+  EncodeTiled fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  // `rows` rows of 2^wlog elements as a rows x (2^wlog elem / 8) array of 8-byte words; a box is
+  // 64 rows of 64 elements
+  const cuuint64_t W = 1ull << wlog;
+  const cuuint64_t dims[2] = {W * (cuuint64_t)elem / 8, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {W * (cuuint64_t)elem};
+  const cuuint32_t box[2] = {64u * (cuuint32_t)elem / 8, 64u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(G), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t scratch_tensor_map(CUtensorMap* map, void* base, long long rows, int row_words, int box_words,
                                int box_rows) {
   EncodeTiled fn = encode_tiled();

@@ -55,6 +55,8 @@ namespace pauli {
 
 cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out);
 cudaError_t tiled_tensor_map(CUtensorMap* map, const void* G, int N, int count, int elem);
+// `rows` rows of 2^wlog elements (a shard's block-XOR layout), 64 x 64 boxes (tiled.cu).
+cudaError_t tiled_tensor_map_rows(CUtensorMap* map, const void* G, int wlog, long long rows, int elem);
 // 4D map of the scratch ring's stage-2 chunks (tiled.cu).
 cudaError_t scratch_tensor_map4(CUtensorMap* map, void* base, int chunks, int nr, int slice_words);
 bool tiled_take_stall();
@@ -261,13 +263,22 @@ __device__ __forceinline__ bool wait_released(const volatile int* released, int 
   return false;
 }
 
+// The matrix, or one x-class shard of it (pauli_decompose_xhi): the 2^k stacked blocks of the
+// block-XOR layout (2^N rows of 2^m elements, m = N - k) in, the coefficients of the classes
+// x = xhi | x_lo out, compacted to (z_hi << 2m) | n_lo. The whole matrix is m = N, xhi = 0.
+struct ShardArgs {
+  int m;
+  uint32_t xhi;
+};
+
 // ---------------------------------------------------------------------- copy warp --
-template <int N, class AR>
+template <int N, class AR, bool SHARD>
 __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int count, TiledCtrl* ws, Shared& sh,
-                         uint32_t buf0) {
+                         uint32_t buf0, ShardArgs sa) {
   using GE = Geo<N>;
   constexpr uint32_t D = 1u << N;
-  constexpr int nb = 1 << (N - kCB);
+  const int nbl = SHARD ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks of 64 classes per matrix (or shard)
+  const uint32_t wmask = SHARD ? (1u << sa.m) - 1u : ~0u;
   constexpr uint32_t kTileBytes = 64u * 64u * sizeof(typename AR::Raw);
   constexpr int kX = (int)sizeof(typename AR::Raw) / 8;  // map words per matrix element
   const int blocks = nb * count;
@@ -336,9 +347,9 @@ __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int c
     sh.use_of[buf] = use;
     if (it.s1) {
       mbar_arrive_tx(full, kTileBytes);
-      const uint32_t k = (uint32_t)(it.b % nb), row0 = (uint32_t)it.j << kTB;
-      const uint32_t colb = (row0 ^ (k << kCB)) & ~63u;
-      tma_2d(dst, gmap, (int)colb * kX, (int)((uint32_t)(it.b / nb) * D + row0), full, pol_first);
+      const uint32_t k = (uint32_t)(it.b & (nb - 1)), row0 = (uint32_t)it.j << kTB;
+      const uint32_t colb = (row0 ^ (k << kCB)) & wmask & ~63u;  // column of the row's block (shard: in it)
+      tma_2d(dst, gmap, (int)colb * kX, (int)((uint32_t)(it.b >> nbl) * D + row0), full, pol_first);
     } else {
       mbar_arrive_tx(full, (uint32_t)(GE::kChunk + GE::kEOct + 32));
       // one 4D box: the 8 warps' transform groups x all tiles of chunk j, warp slices contiguous
@@ -472,10 +483,10 @@ __host__ __device__ constexpr uint32_t s2_hreg(int j) {
 // Warp p of stage-2 item jj of block k: transforms p TPW .. p TPW + TPW - 1 of the chunk, held
 // at `region` as [R][TPW] 16-byte entries; Es = E[R][c8] of the chunk's octet, emax8 = the
 // octet's tagged class maxima.
-template <int N, class AR>
+template <int N, class AR, bool SHARD = false>
 __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32_t emax8, uint32_t lane,
                                             uint32_t p, uint32_t k, uint32_t jj, void* __restrict__ out,
-                                            unsigned long long obase, uint64_t pol_out) {
+                                            unsigned long long obase, uint64_t pol_out, ShardArgs sa = ShardArgs{N, 0u}) {
   using GE = Geo<N>;
   constexpr int RLB = GE::RLB, LTPW = GE::LTPW;
   constexpr uint32_t TPW = GE::TPW;
@@ -484,7 +495,7 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
   const uint32_t t = p * TPW + tt, c8 = t & 7u, wlo = t >> 3;
   const uint32_t o = jj / GE::NCH, whi = jj % GE::NCH;
   const uint32_t w = (whi << LTPW) | wlo;
-  const uint32_t x = (k << kCB) | (o << 3) | c8;
+  const uint32_t x = (SHARD ? sa.xhi : 0u) | (k << kCB) | (o << 3) | c8;
   typename AR::Elem v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
@@ -538,17 +549,29 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
   BitSum<q0, q1, q2, q3> xo;
   xo.init(x);
   const uint32_t ko = (uint32_t)__popc(x & zl);
+  if constexpr (SHARD) {
+    // compact index of the shard's output: n's low 2m bits, then the top z bits
+    const uint32_t lomask = (uint32_t)((1ull << (2 * sa.m)) - 1ull);
 #pragma unroll
-  for (int j = 0; j < 16; ++j) AR::store_hint(out, ao.at(s2_hreg<N>(j) << kCB), v[j], cv, ko + xo.at(j), pol_out);
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t z = zl | (s2_hreg<N>(j) << kCB);
+      const uint32_t n = (uint32_t)(ao.at(s2_hreg<N>(j) << kCB) - obase);
+      const unsigned long long idx = obase + ((n & lomask) | ((z >> sa.m) << (2 * sa.m)));
+      AR::store_hint(out, idx, v[j], cv, ko + xo.at(j), pol_out);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) AR::store_hint(out, ao.at(s2_hreg<N>(j) << kCB), v[j], cv, ko + xo.at(j), pol_out);
+  }
 }
 
 // ---------------------------------------------------------------------- consumers --
-template <int N, class AR>
+template <int N, class AR, bool SHARD>
 __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Shared& sh, uint32_t buf0,
-                         uint32_t warp, uint32_t lane) {
+                         uint32_t warp, uint32_t lane, ShardArgs sa) {
   using GE = Geo<N>;
   constexpr uint32_t D = 1u << N;
-  constexpr int nb = 1 << (N - kCB);
+  const int nbl = SHARD ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks per matrix (or shard)
   const uint32_t team = warp / kTeamWarps, p = warp % kTeamWarps;
   const int blocks = nb * count;
   const uint64_t pol_keep = policy_evict_last(), pol_first = policy_evict_first();
@@ -579,10 +602,10 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
     } else {
       // the slot's data of this item is in shared memory: a relaxed count suffices
       if (p == 0 && lane == 0) red_relaxed_add(&ws->s2_done[s], 1);
-      stage2_warp<N, AR>(addr + p * kWarpBytes, addr + (uint32_t)GE::kChunk, addr + (uint32_t)(GE::kChunk + GE::kEOct),
-                         lane, p,
-                         (uint32_t)(it.b % nb), (uint32_t)it.j, out, (unsigned long long)(it.b / nb) * D * D,
-                         pol_first);
+      stage2_warp<N, AR, SHARD>(addr + p * kWarpBytes, addr + (uint32_t)GE::kChunk,
+                                addr + (uint32_t)(GE::kChunk + GE::kEOct), lane, p, (uint32_t)(it.b & (nb - 1)),
+                                (uint32_t)it.j, out, (unsigned long long)(it.b >> nbl) * D * (SHARD ? 1ull << sa.m : D),
+                                pol_first, sa);
     }
     // the warp is done with the buffer (measured faster than handing it back right after its
     // last shared-memory access) and has issued its stores
@@ -595,10 +618,10 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
   }
 }
 
-template <int N, class AR>
+template <int N, class AR, bool SHARD>
 __global__ void __launch_bounds__(kThreads, 1)
     twostage_kernel(const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap smap,
-                    void* __restrict__ out, int count, TiledCtrl* ws) {
+                    void* __restrict__ out, int count, TiledCtrl* ws, ShardArgs sa) {
   extern __shared__ __align__(1024) char bufs[];
   __shared__ Shared sh;
   const uint32_t t = threadIdx.x, warp = t >> 5, lane = t & 31u;
@@ -618,10 +641,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp < (uint32_t)kConsumerWarps) {
     regs_inc<kConsumerRegs>();
-    consumer<N, AR>(out, count, ws, sh, buf0, warp, lane);
+    consumer<N, AR, SHARD>(out, count, ws, sh, buf0, warp, lane, sa);
   } else {
     regs_dec<kHelperRegs>();
-    if (warp == (uint32_t)kConsumerWarps && lane == 0) producer<N, AR>(&gmap, &smap, count, ws, sh, buf0);
+    if (warp == (uint32_t)kConsumerWarps && lane == 0) producer<N, AR, SHARD>(&gmap, &smap, count, ws, sh, buf0, sa);
     if (warp == (uint32_t)kConsumerWarps + 1 && lane == 0) releaser(ws, sh);
   }
   __syncwarp();
@@ -636,18 +659,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int N, class AR>
-cudaError_t launch_t(const void* G, int count, void* out, cudaStream_t st) {
+// SHARD: G is the block-XOR layout of shard sa (one matrix, count = 1); else sa = {N, 0}.
+template <int N, class AR, bool SHARD = false>
+cudaError_t launch_t(const void* G, int count, void* out, cudaStream_t st, ShardArgs sa = ShardArgs{N, 0u}) {
   using GE = Geo<N>;
   void* ws = nullptr;
   cudaError_t e = tiled_workspace(st, GE::kWorkspace, &ws);
   if (e != cudaSuccess) return e;
   CUtensorMap gmap, smap;
-  e = tiled_tensor_map(&gmap, G, N, count, (int)sizeof(typename AR::Raw));
+  e = SHARD ? tiled_tensor_map_rows(&gmap, G, sa.m, (1ll << N) * count, (int)sizeof(typename AR::Raw))
+            : tiled_tensor_map(&gmap, G, N, count, (int)sizeof(typename AR::Raw));
   if (e != cudaSuccess) return e;
   e = scratch_tensor_map4(&smap, reinterpret_cast<char*>(ws) + GE::kPBase, GE::NS * GE::NR, GE::NR, GE::TPW * 2);
   if (e != cudaSuccess) return e;
-  auto kern = twostage_kernel<N, AR>;
+  auto kern = twostage_kernel<N, AR, SHARD>;
   constexpr size_t smem = kBufs * GE::kBuf;
   static int grid = 0;  // one CTA per SM
   if (!grid) {
@@ -669,7 +694,7 @@ cudaError_t launch_t(const void* G, int count, void* out, cudaStream_t st) {
     e = cudaMemsetAsync(reinterpret_cast<char*>(ws) + offsetof(TiledCtrl, stall), 1, 1, st);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, kThreads, smem, st>>>(gmap, smap, out, count, reinterpret_cast<TiledCtrl*>(ws));
+  kern<<<grid, kThreads, smem, st>>>(gmap, smap, out, count, reinterpret_cast<TiledCtrl*>(ws), sa);
   return cudaGetLastError();
 }
 
@@ -679,6 +704,19 @@ cudaError_t launch_n(const void* G, int N, int count, void* out, cudaStream_t st
     case 12: return launch_t<12, AR>(G, count, out, st);
     case 13: return launch_t<13, AR>(G, count, out, st);
     case 14: return launch_t<14, AR>(G, count, out, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+// x-class shard x_hi of 2^k from its block-XOR layout L (needs N - k >= 6).
+template <class AR>
+cudaError_t launch_xhi_n(const void* L, int N, int k, uint32_t x_hi, void* out, cudaStream_t st) {
+  const ShardArgs sa{N - k, x_hi << (N - k)};
+  if (N - k < kCB) return cudaErrorNotSupported;
+  switch (N) {
+    case 12: return launch_t<12, AR, true>(L, 1, out, st, sa);
+    case 13: return launch_t<13, AR, true>(L, 1, out, st, sa);
+    case 14: return launch_t<14, AR, true>(L, 1, out, st, sa);
     default: return cudaErrorNotSupported;
   }
 }

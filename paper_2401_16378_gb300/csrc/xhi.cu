@@ -14,6 +14,9 @@
 //     into out: out[r_hi 4^m + n_lo] = c_{B(r_hi)}(n_lo)), then
 //  2. in place, a k-bit Walsh-Hadamard transform over r_hi at every n_lo, the phase
 //     i^popc(x_hi & z_hi) and the exact scale 2^-k: out[z_hi 4^m + n_lo] = c(x, z).
+// For N = 12..14 with m >= 6 the two-stage kernel instead runs the whole transform of the shard's
+// classes in one launch, reading the layout's tiles and writing the compact index directly
+// (twostage_impl.cuh, ShardArgs): the same arithmetic, bit for bit, as the full decomposition.
 // Step 2 runs in passes of up to 4 bits of r_hi (registers hold 2^4 values), the phase and
 // scale in the last pass. Its sums are FP64 for both dtypes (complex64 values are widened and
 // rounded once per pass).
@@ -118,6 +121,14 @@ cudaError_t launch_pass_b(int B, void* out, int m, int k, int b0, bool last, uin
 }
 
 }  // namespace
+
+cudaError_t twostage_launch_xhi_c128(const void* L, int N, int k, uint32_t x_hi, void* out, cudaStream_t st);
+cudaError_t twostage_launch_xhi_c64(const void* L, int N, int k, uint32_t x_hi, void* out, cudaStream_t st);
+
+cudaError_t twostage_launch_xhi(const void* L, int N, int k, uint32_t x_hi, bool c64, void* out, cudaStream_t s) {
+  if (N < 12 || N > 14 || N - k < 6 || (reinterpret_cast<uintptr_t>(L) & 15u)) return cudaErrorNotSupported;
+  return c64 ? twostage_launch_xhi_c64(L, N, k, x_hi, out, s) : twostage_launch_xhi_c128(L, N, k, x_hi, out, s);
+}
 
 cudaError_t launch_xhi_combine(void* out, int N, int k, uint32_t x_hi, bool c64, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;

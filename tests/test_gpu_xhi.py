@@ -103,3 +103,23 @@ def test_layout_copy_of_unaligned_views(dtype):
         for r in range(D):
             cb = (r >> (N - k)) ^ g
             assert np.array_equal(L[r], G_h[r, cb * M:(cb + 1) * M])
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("N,k", [(12, 1), (13, 2), (14, 3), (12, 6)])
+def test_two_stage_shard_equals_the_full_decomposition(N, k, dtype):
+    """N = 12..14 with N - k >= 6: one two-stage launch per shard, reading the layout's tiles and
+    writing the compact order -- the same classes, tiles and scales as the full decomposition, so
+    the same bits (complex64 too: the same compensated grids)."""
+    G_h = workloads.gaussian_complex(N, 700 + N + k, NP[dtype])
+    G = torch.from_numpy(G_h).cuda()
+    pg.set_variant(N, dtype, "decompose", "twostage")
+    try:
+        full = pg.decompose(G).cpu().numpy()
+    finally:
+        pg.set_variant(N, dtype, "decompose", "default")
+    L = torch.empty((1 << N, 1 << (N - k)), dtype=dtype, device="cuda")
+    for g in (0, (1 << k) - 1, (1 << k) // 3):
+        pg.xhi_layout(G, k, g, out=L)
+        o = pg.decompose_xhi(L, N, k, g).cpu().numpy()
+        np.testing.assert_array_equal(o, full[shard.shard_indices(N, k, g).astype(np.int64)])
