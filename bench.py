@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--hermitian", action="store_true",
                    help="with --profile-batch: the Hermitian (upper-triangle, real output) plan")
     p.add_argument("--forms-only", default="",
-                   help="comma list of secondary forms (n6, n12, c64, batched, adjoint, xhi) to run alone, "
+                   help="comma list of secondary forms (n6, n12, c64, batched, adjoint, xhi, h14) to run alone, "
                         "without the timed step; prints their JSON")
     return p.parse_args()
 
@@ -484,7 +484,35 @@ def secondary_forms(pg, workloads, dev, stream, G14=None, only=None):
         adjoint_form(pg, workloads, dev, oracle, timed, forms)
     if want("xhi") and G14 is not None:
         xhi_form(pg, workloads, dev, oracle, timed, forms, G14)
+    if want("h14"):
+        h14_form(pg, workloads, dev, oracle, timed, forms)
     return forms
+
+
+def h14_form(pg, workloads, dev, oracle, timed, forms):
+    """N=14 Hermitian complex128 matrix: real parts from the full matrix (24 B per coefficient)
+    and from its upper triangle only (two-stage upper-triangle mode, 16 B per coefficient)."""
+    import torch
+
+    N = 14
+    H = workloads.hermitian_complex(N, workloads.SEEDS["n12_herm"] + 2)
+    h = torch.from_numpy(H).to(dev)
+    r_full = torch.empty(4 ** N, dtype=torch.float64, device=dev)
+    r_up = torch.empty_like(r_full)
+    ms_full = timed(lambda: pg.decompose_hermitian(h, out=r_full), 10)
+    ms_up = timed(lambda: pg.decompose_hermitian(h, out=r_up, upper=True), 10)
+    same = bool(torch.equal(r_full, r_up))
+    idx = workloads.sample_indices(N, 1414, k=512)
+    err = float(np.max(np.abs(r_up.cpu().numpy()[idx.astype(np.int64)] - oracle.decompose_at(H, idx).real))
+                / np.max(np.abs(H)))
+    forms["n14_hermitian_real_c128"] = {"ms": ms_full, "coeffs_per_s": 4 ** N / (ms_full * 1e-3),
+                                        "hbm_gbs_algorithmic": 4 ** N * 24 / (ms_full * 1e-3) / 1e9}
+    forms["n14_hermitian_upper_c128"] = {"ms": ms_up, "coeffs_per_s": 4 ** N / (ms_up * 1e-3),
+                                         "hbm_gbs_algorithmic": 4 ** N * 16 / (ms_up * 1e-3) / 1e9,
+                                         "bit_identical_to_full_read": same, "max_err_rel": err,
+                                         "sample": "512 seeded coefficients vs the oracle",
+                                         "reads": "diagonal and upper triangle of G only"}
+    del h, r_full, r_up
 
 
 def xhi_form(pg, workloads, dev, oracle, timed, forms, G14):

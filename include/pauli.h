@@ -130,9 +130,14 @@ int pauli_decompose_hermitian(const void* G, int N, int count, int dtype, void* 
  * Walsh-Hadamard transform over the other N - 1 row bits gives two real coefficients per
  * value: c(x, z) = 2^(1-N) Re(V[z without bit h] i^popc(x & z)) for z_h = 0 and 1. So the
  * XOR-diagonal kernel reads half of G and writes reals: 16 bytes per complex128 coefficient
- * instead of 32. N <= 12 (PAULI_ERR_UNSUPPORTED above); the XOR-diagonal kernel covers N 7..12,
- * smaller N and PAULI_PLAIN take the per-coefficient sum with the lower triangle read through
- * its mirror. Arguments as for pauli_decompose_hermitian. */
+ * instead of 32. The XOR-diagonal kernel covers N 7..12; at N = 13, 14 (PAULI_AUTO or
+ * PAULI_XORDIAG; count <= 1024, G 16-byte aligned) the two-stage kernel runs in an
+ * upper-triangle mode: a 64 x 64 tile below the diagonal is loaded from its mirror above and
+ * read transposed and conjugated, diagonal tiles mirror their own lower halves, so half of G is
+ * read (the full transform is still computed) and reals are written; for Hermitian G the
+ * values equal pauli_decompose_hermitian's in the same launch shape bit for bit. Smaller N and
+ * PAULI_PLAIN take the per-coefficient sum with the lower triangle read through its mirror;
+ * N > 14 is PAULI_ERR_UNSUPPORTED. Arguments as for pauli_decompose_hermitian. */
 int pauli_decompose_hermitian_upper(const void* G, int N, int count, int dtype, void* out_re, int method,
                                     void* stream);
 

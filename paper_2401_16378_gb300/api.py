@@ -120,7 +120,7 @@ def pauli_decompose_hermitian(G: torch.Tensor, out: torch.Tensor | None = None, 
                               upper: bool = False) -> torch.Tensor:
     """Re c_n for a (..., 2^N, 2^N) complex CUDA tensor (all of c_n when G is Hermitian); returns
     a real (..., 4^N) tensor of G's precision. upper=True: G is Hermitian and only its upper
-    triangle (and the diagonal's real parts) is read -- half the bytes (N <= 12)."""
+    triangle (and the diagonal's real parts) is read -- half the bytes (N <= 14)."""
     _device_tensor(G, "G")
     N = _qubits_of_matrix(G)
     count = G.numel() // (4 ** N)

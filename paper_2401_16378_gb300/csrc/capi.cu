@@ -283,11 +283,19 @@ int pauli_decompose_hermitian_upper(const void* G, int N, int count, int dtype, 
   if (st) return st;
   if (method != PAULI_AUTO && method != PAULI_PLAIN && method != PAULI_XORDIAG)
     return fail(PAULI_ERR_ARG, "method %d is not a pauli_method", method);
-  if (N > 12) return fail(PAULI_ERR_UNSUPPORTED, "pauli_decompose_hermitian_upper is built for N <= 12, not N = %d", N);
+  if (N > 14) return fail(PAULI_ERR_UNSUPPORTED, "pauli_decompose_hermitian_upper is built for N <= 14, not N = %d", N);
   if (method == PAULI_XORDIAG && N < 7)
     return fail(PAULI_ERR_UNSUPPORTED, "the upper-triangle XOR-diagonal kernel starts at N = 7");
-  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
   const bool c64 = dtype == PAULI_C64;
+  if (N >= 13 && method != PAULI_PLAIN) {  // the two-stage kernel in its upper-triangle mode
+    if (count > 1024 || ((uintptr_t)G & 15u))
+      return fail(PAULI_ERR_UNSUPPORTED, "the upper-triangle two-stage kernel takes count <= 1024 and 16-byte aligned G");
+    if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
+    cudaError_t e = pauli::twostage_launch_upper(G, N, count, c64, out_re, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pauli_decompose_hermitian_upper launch");
+    return PAULI_OK;
+  }
+  if (take_injected_failure()) return fail(PAULI_ERR_CUDA, "injected launch failure (test hook)");
   cudaError_t e = (method == PAULI_PLAIN || N < 7)
                       ? pauli::launch_plain_decompose(G, N, count, c64, out_re, (cudaStream_t)stream, true, true)
                       : pauli::launch_xordiag_herm_upper(G, N, count, c64, out_re, (cudaStream_t)stream);

@@ -16,6 +16,9 @@ cudaError_t launch_xordiag_real(const void* G, int N, long long count, void* out
 cudaError_t launch_plain_decompose_real(const void* G, int N, long long count, void* out, cudaStream_t s);
 // Hermitian G read from its upper triangle, real coefficients, N = 7..12 (xordiag_herm_*.cu).
 cudaError_t launch_xordiag_herm_upper(const void* G, int N, long long count, bool c64, void* out, cudaStream_t s);
+// The same for N = 12..14 with the two-stage kernel in its upper-triangle mode (count <= 1024,
+// G 16-byte aligned; tiled.cu).
+cudaError_t twostage_launch_upper(const void* G, int N, int count, bool c64, void* out, cudaStream_t s);
 // w, g (nullable): compose g w_n c_n instead of c_n.
 cudaError_t launch_plain_compose(const void* c, int N, long long count, bool c64, int scale_exp, void* G,
                                 cudaStream_t s, const void* w = nullptr, const void* g = nullptr);

@@ -7,6 +7,7 @@
 
 #include <cuda.h>
 
+#include "kernels.h"
 #include "tiled.h"
 #include "workspace.h"
 
@@ -25,6 +26,13 @@ cudaError_t twostage_launch_c64(const void*, int, int, void*, cudaStream_t);
 cudaError_t twostage_launch_re_c128(const void*, int, int, void*, cudaStream_t);
 cudaError_t twostage_launch_re_c64(const void*, int, int, void*, cudaStream_t);
 size_t twostage_workspace_bytes_c128(int N);
+cudaError_t twostage_launch_upper_c128(const void*, int, int, void*, cudaStream_t);
+cudaError_t twostage_launch_upper_c64(const void*, int, int, void*, cudaStream_t);
+
+cudaError_t twostage_launch_upper(const void* G, int N, int count, bool c64, void* out, cudaStream_t s) {
+  if (!tiled_supported(N) || count < 1 || count > 1024) return cudaErrorNotSupported;
+  return c64 ? twostage_launch_upper_c64(G, N, count, out, s) : twostage_launch_upper_c128(G, N, count, out, s);
+}
 
 // The first buffer of a stream is sized for every N, so that it is never replaced.
 cudaError_t tiled_workspace(cudaStream_t st, size_t bytes, void** out) {

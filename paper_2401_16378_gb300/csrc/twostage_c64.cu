@@ -6,6 +6,9 @@ namespace pauli {
 cudaError_t twostage_launch_c64(const void* G, int N, int count, void* out, cudaStream_t st) {
   return ts::launch_n<xd::ArC64X>(G, N, count, out, st);
 }
+cudaError_t twostage_launch_upper_c64(const void* G, int N, int count, void* out, cudaStream_t st) {
+  return ts::launch_upper_n<xd::ReOut<xd::ArC64X>>(G, N, count, out, st);
+}
 cudaError_t twostage_launch_xhi_c64(const void* L, int N, int k, uint32_t x_hi, void* out, cudaStream_t st) {
   return ts::launch_xhi_n<xd::ArC64X>(L, N, k, x_hi, out, st);
 }

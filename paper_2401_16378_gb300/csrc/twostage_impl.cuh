@@ -270,15 +270,20 @@ struct ShardArgs {
   int m;
   uint32_t xhi;
 };
+// Kernel modes: the whole matrix, one x-class shard, a Hermitian matrix read from its upper
+// triangle (a tile below the diagonal is loaded from its mirror above and read transposed and
+// conjugated; the diagonal tiles mirror their own lower halves; diagonal entries count with
+// their real parts only).
+constexpr int kWhole = 0, kShard = 1, kUpper = 2;
 
 // ---------------------------------------------------------------------- copy warp --
-template <int N, class AR, bool SHARD>
+template <int N, class AR, int MODE>
 __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int count, TiledCtrl* ws, Shared& sh,
                          uint32_t buf0, ShardArgs sa) {
   using GE = Geo<N>;
   constexpr uint32_t D = 1u << N;
-  const int nbl = SHARD ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks of 64 classes per matrix (or shard)
-  const uint32_t wmask = SHARD ? (1u << sa.m) - 1u : ~0u;
+  const int nbl = (MODE == kShard) ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks of 64 classes per matrix (or shard)
+  const uint32_t wmask = (MODE == kShard) ? (1u << sa.m) - 1u : ~0u;
   constexpr uint32_t kTileBytes = 64u * 64u * sizeof(typename AR::Raw);
   constexpr int kX = (int)sizeof(typename AR::Raw) / 8;  // map words per matrix element
   const int blocks = nb * count;
@@ -349,7 +354,11 @@ __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int c
       mbar_arrive_tx(full, kTileBytes);
       const uint32_t k = (uint32_t)(it.b & (nb - 1)), row0 = (uint32_t)it.j << kTB;
       const uint32_t colb = (row0 ^ (k << kCB)) & wmask & ~63u;  // column of the row's block (shard: in it)
-      tma_2d(dst, gmap, (int)colb * kX, (int)((uint32_t)(it.b >> nbl) * D + row0), full, pol_first);
+      const uint32_t mrow = (uint32_t)(it.b >> nbl) * D;
+      if (MODE == kUpper && colb < row0)  // below the diagonal: the mirror tile, read transposed
+        tma_2d(dst, gmap, (int)row0 * kX, (int)(mrow + colb), full, pol_first);
+      else
+        tma_2d(dst, gmap, (int)colb * kX, (int)(mrow + row0), full, pol_first);
     } else {
       mbar_arrive_tx(full, (uint32_t)(GE::kChunk + GE::kEOct + 32));
       // one 4D box: the 8 warps' transform groups x all tiles of chunk j, warp slices contiguous
@@ -384,9 +393,10 @@ __device__ void releaser(TiledCtrl* ws, Shared& sh) {
 // ---------------------------------------------------------------------- stage 1 --
 // Warp o of a stage-1 item: masks 8o..8o+7 of the tile at `tile` (element (i, col) at slot
 // 64 i + col, col = i ^ c for mask c), output to the slot's P and E.
-template <int N, class AR>
+template <int N, class AR, int MODE = kWhole>
 __device__ __forceinline__ void stage1_warp(uint32_t tile, uint32_t lane, uint32_t o, char* P, uint32_t* Eslot,
-                                            TiledCtrl* ws, int s, int gen, uint32_t R, uint64_t pol_keep) {
+                                            TiledCtrl* ws, int s, int gen, uint32_t R, uint64_t pol_keep,
+                                            uint32_t k = 0u) {
   using GE = Geo<N>;
   constexpr uint32_t ES = sizeof(typename AR::Raw);
   using SB = S1Bits<ES>;
@@ -398,14 +408,27 @@ __device__ __forceinline__ void stage1_warp(uint32_t tile, uint32_t lane, uint32
   const uint32_t sa = slot(ua), xa = slot(SB::xrow(ua)), xb = slot(SB::xrow(ub));
   typename AR::Raw raw[16];
   uint32_t emax = 0;
+  // upper-triangle mode: a tile below the diagonal holds the mirror tile, whose element (col, v)
+  // is the conjugate of (v, col); in a diagonal tile (k = 0) the entries below its diagonal are
+  // read the same way from the tile itself, and the diagonal's imaginary parts are dropped.
+  // slot of (col, v) = slot of (v, col) ^ c ^ (c << 6), col = v ^ c
+  const bool below = MODE == kUpper && ((R << kTB) ^ (k << kCB)) < (R << kTB);
+  const bool diag = MODE == kUpper && k == 0u;
+  const uint32_t hc = c ? 31u - (uint32_t)__clz(c) : 32u;  // top set bit of the mask (diagonal tiles)
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const uint32_t a = tile + (sa ^ sreg(reg_a<SB>(j))) * ES;
+    const uint32_t v = ua ^ reg_a<SB>(j);
+    const bool mirror = below || (diag && hc < 32u && ((v >> hc) & 1u));  // element (v, v ^ c) lies below
+    const uint32_t a = tile + ((sa ^ sreg(reg_a<SB>(j))) ^ (mirror ? c | (c << 6) : 0u)) * ES;
     if constexpr (ES == 16) {
       raw[j] = AR::raw_unpack(lds128(a));
     } else {
       const uint2 q = lds64(a);
       raw[j] = AR::raw_unpack(make_uint4(q.x, q.y, 0u, 0u));
+    }
+    if (MODE == kUpper) {
+      if (mirror) raw[j] = AR::conj(raw[j]);
+      if (diag && c == 0u) raw[j] = AR::real_part(raw[j]);
     }
     emax = max(emax, AR::exp_key(raw[j]));
   }
@@ -483,7 +506,7 @@ __host__ __device__ constexpr uint32_t s2_hreg(int j) {
 // Warp p of stage-2 item jj of block k: transforms p TPW .. p TPW + TPW - 1 of the chunk, held
 // at `region` as [R][TPW] 16-byte entries; Es = E[R][c8] of the chunk's octet, emax8 = the
 // octet's tagged class maxima.
-template <int N, class AR, bool SHARD = false>
+template <int N, class AR, int MODE = 0>
 __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32_t emax8, uint32_t lane,
                                             uint32_t p, uint32_t k, uint32_t jj, void* __restrict__ out,
                                             unsigned long long obase, uint64_t pol_out, ShardArgs sa = ShardArgs{N, 0u}) {
@@ -495,7 +518,7 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
   const uint32_t t = p * TPW + tt, c8 = t & 7u, wlo = t >> 3;
   const uint32_t o = jj / GE::NCH, whi = jj % GE::NCH;
   const uint32_t w = (whi << LTPW) | wlo;
-  const uint32_t x = (SHARD ? sa.xhi : 0u) | (k << kCB) | (o << 3) | c8;
+  const uint32_t x = ((MODE == kShard) ? sa.xhi : 0u) | (k << kCB) | (o << 3) | c8;
   typename AR::Elem v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
@@ -549,7 +572,7 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
   BitSum<q0, q1, q2, q3> xo;
   xo.init(x);
   const uint32_t ko = (uint32_t)__popc(x & zl);
-  if constexpr (SHARD) {
+  if constexpr (MODE == kShard) {
     // compact index of the shard's output: n's low 2m bits, then the top z bits
     const uint32_t lomask = (uint32_t)((1ull << (2 * sa.m)) - 1ull);
 #pragma unroll
@@ -566,12 +589,12 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
 }
 
 // ---------------------------------------------------------------------- consumers --
-template <int N, class AR, bool SHARD>
+template <int N, class AR, int MODE>
 __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Shared& sh, uint32_t buf0,
                          uint32_t warp, uint32_t lane, ShardArgs sa) {
   using GE = Geo<N>;
   constexpr uint32_t D = 1u << N;
-  const int nbl = SHARD ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks per matrix (or shard)
+  const int nbl = (MODE == kShard) ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks per matrix (or shard)
   const uint32_t team = warp / kTeamWarps, p = warp % kTeamWarps;
   const int blocks = nb * count;
   const uint64_t pol_keep = policy_evict_last(), pol_first = policy_evict_first();
@@ -597,14 +620,14 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
     const int s = it.b % GE::NS, gen = it.b / GE::NS;
     const uint32_t addr = buf0 + (uint32_t)(buf * GE::kBuf);
     if (it.s1) {
-      stage1_warp<N, AR>(addr, lane, p, P0 + (size_t)s * GE::kSlotP,
-                         E0 + (size_t)s * (GE::kSlotE / 4), ws, s, gen, (uint32_t)it.j, pol_keep);
+      stage1_warp<N, AR, MODE>(addr, lane, p, P0 + (size_t)s * GE::kSlotP, E0 + (size_t)s * (GE::kSlotE / 4), ws, s,
+                               gen, (uint32_t)it.j, pol_keep, (uint32_t)(it.b & (nb - 1)));
     } else {
       // the slot's data of this item is in shared memory: a relaxed count suffices
       if (p == 0 && lane == 0) red_relaxed_add(&ws->s2_done[s], 1);
-      stage2_warp<N, AR, SHARD>(addr + p * kWarpBytes, addr + (uint32_t)GE::kChunk,
+      stage2_warp<N, AR, MODE>(addr + p * kWarpBytes, addr + (uint32_t)GE::kChunk,
                                 addr + (uint32_t)(GE::kChunk + GE::kEOct), lane, p, (uint32_t)(it.b & (nb - 1)),
-                                (uint32_t)it.j, out, (unsigned long long)(it.b >> nbl) * D * (SHARD ? 1ull << sa.m : D),
+                                (uint32_t)it.j, out, (unsigned long long)(it.b >> nbl) * D * ((MODE == kShard) ? 1ull << sa.m : D),
                                 pol_first, sa);
     }
     // the warp is done with the buffer (measured faster than handing it back right after its
@@ -618,7 +641,7 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
   }
 }
 
-template <int N, class AR, bool SHARD>
+template <int N, class AR, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     twostage_kernel(const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap smap,
                     void* __restrict__ out, int count, TiledCtrl* ws, ShardArgs sa) {
@@ -641,10 +664,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp < (uint32_t)kConsumerWarps) {
     regs_inc<kConsumerRegs>();
-    consumer<N, AR, SHARD>(out, count, ws, sh, buf0, warp, lane, sa);
+    consumer<N, AR, MODE>(out, count, ws, sh, buf0, warp, lane, sa);
   } else {
     regs_dec<kHelperRegs>();
-    if (warp == (uint32_t)kConsumerWarps && lane == 0) producer<N, AR, SHARD>(&gmap, &smap, count, ws, sh, buf0, sa);
+    if (warp == (uint32_t)kConsumerWarps && lane == 0) producer<N, AR, MODE>(&gmap, &smap, count, ws, sh, buf0, sa);
     if (warp == (uint32_t)kConsumerWarps + 1 && lane == 0) releaser(ws, sh);
   }
   __syncwarp();
@@ -659,20 +682,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// SHARD: G is the block-XOR layout of shard sa (one matrix, count = 1); else sa = {N, 0}.
-template <int N, class AR, bool SHARD = false>
+// MODE kShard: G is the block-XOR layout of shard sa (one matrix, count = 1); else sa = {N, 0}.
+// MODE kUpper: G is Hermitian and read from its upper triangle.
+template <int N, class AR, int MODE = 0>
 cudaError_t launch_t(const void* G, int count, void* out, cudaStream_t st, ShardArgs sa = ShardArgs{N, 0u}) {
   using GE = Geo<N>;
   void* ws = nullptr;
   cudaError_t e = tiled_workspace(st, GE::kWorkspace, &ws);
   if (e != cudaSuccess) return e;
   CUtensorMap gmap, smap;
-  e = SHARD ? tiled_tensor_map_rows(&gmap, G, sa.m, (1ll << N) * count, (int)sizeof(typename AR::Raw))
+  e = (MODE == kShard) ? tiled_tensor_map_rows(&gmap, G, sa.m, (1ll << N) * count, (int)sizeof(typename AR::Raw))
             : tiled_tensor_map(&gmap, G, N, count, (int)sizeof(typename AR::Raw));
   if (e != cudaSuccess) return e;
   e = scratch_tensor_map4(&smap, reinterpret_cast<char*>(ws) + GE::kPBase, GE::NS * GE::NR, GE::NR, GE::TPW * 2);
   if (e != cudaSuccess) return e;
-  auto kern = twostage_kernel<N, AR, SHARD>;
+  auto kern = twostage_kernel<N, AR, MODE>;
   constexpr size_t smem = kBufs * GE::kBuf;
   static int grid = 0;  // one CTA per SM
   if (!grid) {
@@ -708,15 +732,26 @@ cudaError_t launch_n(const void* G, int N, int count, void* out, cudaStream_t st
   }
 }
 
+// Hermitian G read from its upper triangle (real outputs: AR is a ReOut policy).
+template <class AR>
+cudaError_t launch_upper_n(const void* G, int N, int count, void* out, cudaStream_t st) {
+  switch (N) {
+    case 12: return launch_t<12, AR, kUpper>(G, count, out, st);
+    case 13: return launch_t<13, AR, kUpper>(G, count, out, st);
+    case 14: return launch_t<14, AR, kUpper>(G, count, out, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 // x-class shard x_hi of 2^k from its block-XOR layout L (needs N - k >= 6).
 template <class AR>
 cudaError_t launch_xhi_n(const void* L, int N, int k, uint32_t x_hi, void* out, cudaStream_t st) {
   const ShardArgs sa{N - k, x_hi << (N - k)};
   if (N - k < kCB) return cudaErrorNotSupported;
   switch (N) {
-    case 12: return launch_t<12, AR, true>(L, 1, out, st, sa);
-    case 13: return launch_t<13, AR, true>(L, 1, out, st, sa);
-    case 14: return launch_t<14, AR, true>(L, 1, out, st, sa);
+    case 12: return launch_t<12, AR, kShard>(L, 1, out, st, sa);
+    case 13: return launch_t<13, AR, kShard>(L, 1, out, st, sa);
+    case 14: return launch_t<14, AR, kShard>(L, 1, out, st, sa);
     default: return cudaErrorNotSupported;
   }
 }

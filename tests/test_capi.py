@@ -102,7 +102,8 @@ def test_hermitian_and_norm_reject_bad_arguments(lib):
     assert lib.pauli_decompose_hermitian(P(A), 4, 0, C128, P(B), 0, None) == ARG
     assert lib.pauli_decompose_hermitian(P(A), 3, 1, C128, P(B), 2, None) == UNSUP
     assert lib.pauli_decompose_hermitian_upper(P(A), 6, 1, C128, P(B), 2, None) == UNSUP
-    assert lib.pauli_decompose_hermitian_upper(P(1 << 32), 13, 1, C128, P(2 << 32), 0, None) == UNSUP
+    assert lib.pauli_decompose_hermitian_upper(P(1 << 36), 15, 1, C128, P(2 << 36), 0, None) == UNSUP  # N > 14
+    assert lib.pauli_decompose_hermitian_upper(P(1 << 32), 13, 1025, C128, P(1 << 44), 0, None) == UNSUP  # count
     assert lib.pauli_decompose_hermitian_upper(P(A), 4, 1, C128, P(A + 8), 0, None) == ALIAS
     assert lib.pauli_decompose_hermitian_upper(P(A), 4, 1, C128, P(B), 7, None) == ARG
     assert lib.pauli_decompose_real(P(A), 4, 1, C64, P(B), 0, None) == UNSUP
