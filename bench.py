@@ -51,7 +51,8 @@ def parse():
                    help="with --profile: launch the batched plan over the first B matrices of the "
                         "uneven-N batch instead of the N-qubit decomposition")
     p.add_argument("--hermitian", action="store_true",
-                   help="with --profile-batch: the Hermitian (upper-triangle, real output) plan")
+                   help="with --profile: the Hermitian form read from the upper triangle (real "
+                        "output); with --profile-batch: the Hermitian plan")
     p.add_argument("--forms-only", default="",
                    help="comma list of secondary forms (n6, n12, c64, batched, adjoint, xhi, h14) to run alone, "
                         "without the timed step; prints their JSON")
@@ -317,11 +318,17 @@ def run_ours(args):
             G, out = G.to(torch.complex64), torch.empty(ncoef, dtype=torch.complex64, device=dev)
             if args.variant != "default":
                 pg.set_variant(N, torch.complex64, "decompose", args.variant)
+        if args.hermitian:
+            out = torch.empty(ncoef, dtype=torch.float32 if args.dtype == "c64" else torch.float64, device=dev)
+
+            def step():
+                pg.decompose_hermitian(G, out=out, upper=True)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize(dev)
         ms = event_time(step, args.steps, stream)
-        print(json.dumps({"profile": True, "N": N, "dtype": args.dtype, "ms_per_step": ms}), flush=True)
+        print(json.dumps({"profile": True, "N": N, "dtype": args.dtype, "hermitian_upper": args.hermitian,
+                          "ms_per_step": ms}), flush=True)
         return
 
     def barrier():

@@ -391,6 +391,21 @@ __device__ void releaser(TiledCtrl* ws, Shared& sh) {
 }
 
 // ---------------------------------------------------------------------- stage 1 --
+// e -> -e where the lane mask m is all ones, e unchanged where it is zero (exact: fixed-point
+// values stay below 2^62 in magnitude, and a float changes only its sign bit).
+__device__ __forceinline__ void negate_where(ArC128::Elem& e, uint32_t m) {
+  const long long mm = (long long)(int)m;
+  e.re = (e.re ^ mm) - mm;
+  e.im = (e.im ^ mm) - mm;
+}
+__device__ __forceinline__ void negate_where(ArC64::Elem& e, uint32_t m) {
+  const uint32_t sb = m & 0x80000000u;
+  e.rh = __uint_as_float(__float_as_uint(e.rh) ^ sb);
+  e.rl = __uint_as_float(__float_as_uint(e.rl) ^ sb);
+  e.ih = __uint_as_float(__float_as_uint(e.ih) ^ sb);
+  e.il = __uint_as_float(__float_as_uint(e.il) ^ sb);
+}
+
 // Warp o of a stage-1 item: masks 8o..8o+7 of the tile at `tile` (element (i, col) at slot
 // 64 i + col, col = i ^ c for mask c), output to the slot's P and E.
 template <int N, class AR, int MODE = kWhole>
@@ -412,14 +427,22 @@ __device__ __forceinline__ void stage1_warp(uint32_t tile, uint32_t lane, uint32
   // is the conjugate of (v, col); in a diagonal tile (k = 0) the entries below its diagonal are
   // read the same way from the tile itself, and the diagonal's imaginary parts are dropped.
   // slot of (col, v) = slot of (v, col) ^ c ^ (c << 6), col = v ^ c
+  // A mirror read's bank group is set by the row v alone, which a quarter-warp's lanes share, so
+  // on a tile below the diagonal lane c8 reads its rows in the order v ^ c8 (register j holds row
+  // ua ^ reg_a(j) ^ c8, with reg_a(t) = t for t < 8 in both bit assignments): the 8 (16-byte
+  // elements) or 16 (8-byte) lanes of one wavefront then hit distinct banks. A register
+  // transform of inputs permuted by XOR with t is the transform times (-1)^popc(k & t) at output
+  // k, undone after wht_regs by exact negations.
   const bool below = MODE == kUpper && ((R << kTB) ^ (k << kCB)) < (R << kTB);
   const bool diag = MODE == kUpper && k == 0u;
   const uint32_t hc = c ? 31u - (uint32_t)__clz(c) : 32u;  // top set bit of the mask (diagonal tiles)
+  const uint32_t rot = below ? c8 : 0u;
+  const uint32_t sbase = below ? sa ^ sreg(rot) ^ c ^ (c << 6) : sa;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const uint32_t v = ua ^ reg_a<SB>(j);
+    const uint32_t v = ua ^ reg_a<SB>(j) ^ rot;
     const bool mirror = below || (diag && hc < 32u && ((v >> hc) & 1u));  // element (v, v ^ c) lies below
-    const uint32_t a = tile + ((sa ^ sreg(reg_a<SB>(j))) ^ (mirror ? c | (c << 6) : 0u)) * ES;
+    const uint32_t a = tile + ((sbase ^ sreg(reg_a<SB>(j))) ^ (!below && mirror ? c | (c << 6) : 0u)) * ES;
     if constexpr (ES == 16) {
       raw[j] = AR::raw_unpack(lds128(a));
     } else {
@@ -443,6 +466,14 @@ __device__ __forceinline__ void stage1_warp(uint32_t tile, uint32_t lane, uint32
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = AR::template convert<0>(raw[j], cv, 0u);
   wht_regs<AR, 4, 16>(v);
+  if constexpr (MODE == kUpper) {
+    if (below) {
+      const uint32_t m0 = 0u - (rot & 1u), m1 = 0u - ((rot >> 1) & 1u), m2 = 0u - ((rot >> 2) & 1u);
+#pragma unroll
+      for (int j = 1; j < 16; ++j)
+        if (j & 7) negate_where(v[j], ((j & 1) ? m0 : 0u) ^ ((j & 2) ? m1 : 0u) ^ ((j & 4) ? m2 : 0u));
+    }
+  }
   // exchange within the warp's own slots (the octet's 8 slots of each row): element u goes to
   // the slot of row xrow(u), written in phase A's layout and read in phase B's
   __syncwarp();  // every lane's tile reads are done
