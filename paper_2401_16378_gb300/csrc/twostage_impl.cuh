@@ -289,7 +289,6 @@ __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int c
   const int blocks = nb * count;
   const int n_items = (blocks + GE::LAG) * (GE::n1 + GE::n2);
   const uint64_t pol_first = policy_evict_first();
-  const uint64_t pol_last = MODE == kUpper ? policy_evict_last() : pol_first;
   const volatile int* released = &sh.released;
   char* const E0 = reinterpret_cast<char*>(ws) + GE::kEBase;
   prefetch_tensormap(gmap);
@@ -358,8 +357,6 @@ __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int c
       const uint32_t mrow = (uint32_t)(it.b >> nbl) * D;
       if (MODE == kUpper && colb < row0)  // below the diagonal: the mirror tile, read transposed
         tma_2d(dst, gmap, (int)row0 * kX, (int)(mrow + colb), full, pol_first);
-      else if (MODE == kUpper && colb > row0)  // read again later in this block, as tile (R ^ k)'s mirror
-        tma_2d(dst, gmap, (int)colb * kX, (int)(mrow + row0), full, pol_last);
       else
         tma_2d(dst, gmap, (int)colb * kX, (int)(mrow + row0), full, pol_first);
     } else {
