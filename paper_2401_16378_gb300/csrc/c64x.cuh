@@ -11,14 +11,18 @@
 //    2008).
 //  - stage 1 (6 stages over the tile's rows): q1 = 2^(6 - 24) M1, M1 = 2^(E1 - 126) > every |x| of
 //    the mask in the tile (E1: its largest float exponent field).
-//  - stage 2 (the other N - 6 stages): the high parts of every tile are re-split on the mask's
-//    grid q2 = 2^(N + 1 - 24) Mm (Mm from the largest exponent over all tiles; one bit of headroom
-//    for the re-rounding of the tiles' sums): hi2 = fl(hi + C2) - C2, lo2 = lo + (hi - hi2), where
-//    hi - hi2 is exact (Sterbenz: hi2 is hi rounded to a coarser grid).
+//  - between the stages each stage-1 value is kept as one float per part, fl(hi + lo) (the
+//    scratch ring then holds 8 bytes per value, as G does).
+//  - stage 2 (the other N - 6 stages): each stored value is split again, on the mask's grid
+//    q2 = 2^(N + 1 - 24) Mm (Mm from the largest exponent over all tiles; one bit of headroom
+//    for the rounding of the tiles' sums): hi2 = fl(x + C2) - C2, lo2 = x - hi2, exact.
 //  - output: fl(hi + lo) times the exact 2^-N, times i^k.
 // Error: the high parts are exact; the low parts start below q2 / 2 and FP32 recursive summation of
 // 2^N of them errs by at most about N 2^-24 2^N q2 / 2 = N 2^(2N - 48) Mm in a sum, i.e. N 2^(N - 48) Mm
-// in a coefficient (about 8e-10 Mm at N = 14), below the final rounding of a coefficient to FP32.
+// in a coefficient (about 8e-10 Mm at N = 14). The rounding of the stage-1 values adds at most
+// 2^-24 of each (|x| <= 2^6 Mm) to 2^(N - 6) terms of a sum: 2^-24 Mm in a coefficient in the
+// worst case, of the order of the final rounding of a coefficient to FP32, and much less for
+// values of mixed signs (the errors of independent tiles average out).
 // Inputs of magnitude above about 2^(126 - N) would leave the FP32 range in the sums: the anchor of
 // such a mask is NaN, so all of its outputs are NaN.
 #pragma once
@@ -37,8 +41,15 @@ struct ArC64X : ArC64 {
   __device__ static __forceinline__ Conv make_conv(int N, uint32_t Ekey, int out_scale) {
     return Conv{anchor(Ekey >> 23, out_scale == 0 ? 6 : N + 1), __int_as_float((127 + out_scale) << 23)};
   }
-  // re-split a stage-1 value on the mask's stage-2 grid: hi - hi2 is exact (Sterbenz: hi2 is hi
-  // rounded to a coarser grid)
+  // A stage-1 value as the scratch keeps it: each part's pair (hi, lo) rounded once to a float.
+  __device__ static __forceinline__ uint2 pack_rounded(const Elem& a) {
+    return make_uint2(__float_as_uint(__fadd_rn(a.rh, a.rl)), __float_as_uint(__fadd_rn(a.ih, a.il)));
+  }
+  __device__ static __forceinline__ Elem unpack_rounded(const uint2& q) {
+    return Elem{__uint_as_float(q.x), 0.0f, __uint_as_float(q.y), 0.0f};
+  }
+  // re-split a stage-1 value x = hi + lo on the mask's stage-2 grid: hi2 = fl(hi + C2) - C2 and
+  // hi - hi2 are exact (the split above)
   __device__ static __forceinline__ void regrid(Elem& a, const Conv& cv) {
     float h, r;
     h = __fsub_rn(__fadd_rn(a.rh, cv.anchor), cv.anchor);

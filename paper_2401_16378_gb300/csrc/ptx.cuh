@@ -25,6 +25,10 @@ __device__ __forceinline__ void st_hint(void* a, const uint4& v, uint64_t pol) {
                "r"(v.w), "l"(pol)
                : "memory");
 }
+// 8-byte global store with an L2 cache policy
+__device__ __forceinline__ void st_hint(void* a, const uint2& v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1,%2}, %3;" ::"l"(a), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
+}
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

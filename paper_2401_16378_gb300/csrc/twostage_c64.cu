@@ -17,9 +17,9 @@ cudaError_t twostage_launch_re_c64(const void* G, int N, int count, void* out, c
 }
 size_t twostage_workspace_bytes_c64(int N) {
   switch (N) {
-    case 12: return ts::Geo<12>::kWorkspace;
-    case 13: return ts::Geo<13>::kWorkspace;
-    case 14: return ts::Geo<14>::kWorkspace;
+    case 12: return ts::Geo<12, ts::kScratchEntry<xd::ArC64X>>::kWorkspace;
+    case 13: return ts::Geo<13, ts::kScratchEntry<xd::ArC64X>>::kWorkspace;
+    case 14: return ts::Geo<14, ts::kScratchEntry<xd::ArC64X>>::kWorkspace;
     default: return 0;
   }
 }

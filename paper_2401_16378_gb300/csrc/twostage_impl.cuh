@@ -23,10 +23,12 @@
 //    into its own 8 KiB of the buffer; four stages in registers, an in-place exchange with an
 //    XOR swizzle that keeps both access patterns free of bank conflicts, the remaining L - 4
 //    stages, the phase, the scale and the stores of c(x, z).
-// Scratch layout of a slot (one block of 64 masks): P[chunk jj][R][t] (16-byte entries; chunk
-// jj = o (2^(L-3)) + (w >> (9-L)), transform t = ((w mod 2^(9-L)) << 3) | c8 for mask 8o + c8 and
-// stage-1 output index w), then, after every slot's P, E[slot][o][R][c8] (the exponent key of
-// each mask in each tile). Stage-1 stores are 128- or 256-byte runs of one (chunk, R).
+// Scratch layout of a slot (one block of 64 masks): P[chunk jj][R][t] (chunk jj = o (2^(L-3)) +
+// (w >> (9-L)), transform t = ((w mod 2^(9-L)) << 3) | c8 for mask 8o + c8 and stage-1 output
+// index w), then, after every slot's P, E[slot][o][R][c8] (the exponent key of each mask in each
+// tile). Entries are 16 bytes for complex128 (the int64 pair; stage-1 stores are 128- or 256-byte
+// runs of one (chunk, R)) and 8 bytes for complex64 (each part's compensated pair rounded once
+// to a float: half the ring's bytes and L2 traffic; both stages still sum with compensation).
 //
 // Schedule, dependencies and bounded waits are those of the block-tiled kernel: one persistent
 // CTA per SM; a copy warp takes work items from a global counter in the order S1(block 0) ..
@@ -77,9 +79,13 @@ static_assert(kConsumerWarps * 32 * kConsumerRegs + 128 * kHelperRegs <= kThread
               "the register split fits the launch's 96 registers per thread");
 constexpr int kStatusTimeout = 8;     // PAULI_ERR_TIMEOUT
 constexpr int kStallPolls = 1 << 15;  // the test hook's wait: well under a second
-constexpr uint32_t kWarpBytes = 8192;  // 512 elements x 16 bytes per consumer warp
 
-template <int N>
+// Bytes of one scratch entry: complex128 stage-1 values are int64 pairs (16 bytes); complex64
+// values are stored as one float per part, the compensated pair (hi, lo) rounded once (8 bytes).
+template <class AR>
+constexpr int kScratchEntry = std::is_base_of<ArC64X, AR>::value ? 8 : 16;
+
+template <int N, int SE = 16>
 struct Geo {
   static constexpr int L = N - kTB;      // stage-2 bits
   static constexpr int NR = 1 << L;      // tiles per block = stage-2 items per block
@@ -88,11 +94,17 @@ struct Geo {
   static constexpr int LTPW = 9 - L;     // log2 TPW
   static constexpr int RLB = L - 4;      // tile bits in the lanes at stage 2's first phase
   static constexpr int NCH = NR / 8;     // chunks per octet
-  static constexpr size_t kChunk = 65536;
+  static_assert(SE == 8 || SE == 16, "scratch entries of 8 or 16 bytes");
+  static constexpr size_t kChunk = 4096 * SE;  // bytes of one chunk in the scratch and of its copy
+  static constexpr uint32_t kSlice = 512 * SE;  // one consumer warp's part of a chunk copy
+  // a buffer's chunk area: 4096 16-byte entries (the stage-2 exchange runs on 16-byte entries;
+  // with 8-byte scratch entries warp p's exchange uses its own copied slice and the slice's
+  // twin in the area's upper half)
+  static constexpr size_t kChunkArea = 65536;
   static constexpr size_t kSlotP = (size_t)NR * kChunk;
   static constexpr size_t kSlotE = (size_t)NR * 64 * 4;
   static constexpr size_t kEOct = (size_t)NR * 8 * 4;
-  static constexpr size_t kBuf = kChunk + kEOct + 128;
+  static constexpr size_t kBuf = kChunkArea + kEOct + 128;
   // ring depth and lag, measured: 13 x 4 MiB with a lag of 6 blocks at N = 12 (0.163 ms against
   // 0.180 ms with 6 slots and a lag of 3), 6 x 8 MiB / 3 at N = 13, 4 x 16 MiB / 2 at N = 14 (deeper
   // rings spill from L2 there and are slower)
@@ -280,7 +292,7 @@ constexpr int kWhole = 0, kShard = 1, kUpper = 2;
 template <int N, class AR, int MODE>
 __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int count, TiledCtrl* ws, Shared& sh,
                          uint32_t buf0, ShardArgs sa) {
-  using GE = Geo<N>;
+  using GE = Geo<N, kScratchEntry<AR>>;
   constexpr uint32_t D = 1u << N;
   const int nbl = (MODE == kShard) ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks of 64 classes per matrix (or shard)
   const uint32_t wmask = (MODE == kShard) ? (1u << sa.m) - 1u : ~0u;
@@ -364,9 +376,9 @@ __device__ void producer(const CUtensorMap* gmap, const CUtensorMap* smap, int c
       // one 4D box: the 8 warps' transform groups x all tiles of chunk j, warp slices contiguous
       tma_4d(dst, smap, 0, 0, 0, s * GE::NR + it.j, full, pol_first);
       const int o = it.j / GE::NCH;
-      bulk_g2s(dst + (uint32_t)GE::kChunk, E0 + (size_t)s * GE::kSlotE + (size_t)o * GE::kEOct, (uint32_t)GE::kEOct,
-               full, pol_first);
-      bulk_g2s(dst + (uint32_t)(GE::kChunk + GE::kEOct), &ws->emax[s][o * 8], 32u, full, pol_first);
+      bulk_g2s(dst + (uint32_t)GE::kChunkArea, E0 + (size_t)s * GE::kSlotE + (size_t)o * GE::kEOct,
+               (uint32_t)GE::kEOct, full, pol_first);
+      bulk_g2s(dst + (uint32_t)(GE::kChunkArea + GE::kEOct), &ws->emax[s][o * 8], 32u, full, pol_first);
     }
     sh.issued_use[buf] = use;
     ++use;
@@ -412,7 +424,7 @@ template <int N, class AR, int MODE = kWhole>
 __device__ __forceinline__ void stage1_warp(uint32_t tile, uint32_t lane, uint32_t o, char* P, uint32_t* Eslot,
                                             TiledCtrl* ws, int s, int gen, uint32_t R, uint64_t pol_keep,
                                             uint32_t k = 0u) {
-  using GE = Geo<N>;
+  using GE = Geo<N, kScratchEntry<AR>>;
   constexpr uint32_t ES = sizeof(typename AR::Raw);
   using SB = S1Bits<ES>;
   const uint32_t c8 = lane & 7u, la = lane >> 3;
@@ -508,10 +520,16 @@ __device__ __forceinline__ void stage1_warp(uint32_t tile, uint32_t lane, uint32
   }
   wht_regs<AR, 2, 16>(v);  // register bits 0, 1 hold row bits A0, A1
   // P[chunk][R][t]: chunk = 8o... + (w >> LTPW), t = (w mod TPW) << 3 | c8
-  uint4* Pp = reinterpret_cast<uint4*>(P) + o * (uint32_t)(GE::NCH * GE::NR * GE::TPI) + R * (uint32_t)GE::TPI + c8 +
-              s1_w_off<N>(ub);
+  const uint32_t pe = o * (uint32_t)(GE::NCH * GE::NR * GE::TPI) + R * (uint32_t)GE::TPI + c8 + s1_w_off<N>(ub);
+  if constexpr (kScratchEntry<AR> == 16) {
+    uint4* Pp = reinterpret_cast<uint4*>(P) + pe;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) st_hint(Pp + s1_w_off<N>(reg_b<SB>(j)), AR::pack(v[j]), pol_keep);
+    for (int j = 0; j < 16; ++j) st_hint(Pp + s1_w_off<N>(reg_b<SB>(j)), AR::pack(v[j]), pol_keep);
+  } else {
+    uint2* Pp = reinterpret_cast<uint2*>(P) + pe;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) st_hint(Pp + s1_w_off<N>(reg_b<SB>(j)), AR::pack_rounded(v[j]), pol_keep);
+  }
   if (la == 0u) {
     Eslot[(o * (uint32_t)GE::NR + R) * 8u + c8] = Ekey;
     if constexpr (AR::kScaled) red_max(&ws->emax[s][c], ((uint32_t)(gen + 1) << 11) | key_exp<AR>(Ekey));
@@ -535,13 +553,16 @@ __host__ __device__ constexpr uint32_t s2_hreg(int j) {
 }
 
 // Warp p of stage-2 item jj of block k: transforms p TPW .. p TPW + TPW - 1 of the chunk, held
-// at `region` as [R][TPW] 16-byte entries; Es = E[R][c8] of the chunk's octet, emax8 = the
-// octet's tagged class maxima.
+// at `region` as [R][TPW] scratch entries; Es = E[R][c8] of the chunk's octet, emax8 = the
+// octet's tagged class maxima. The exchange runs on 16-byte entries: in `region` itself (16-byte
+// scratch entries), or (8-byte entries: `region` holds 4 KiB) entries 0..255 in `region` and
+// 256..511 in `twin`, this warp's 4 KiB in the upper half of the chunk area.
 template <int N, class AR, int MODE = 0>
-__device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32_t emax8, uint32_t lane,
+__device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t twin, uint32_t Es, uint32_t emax8, uint32_t lane,
                                             uint32_t p, uint32_t k, uint32_t jj, void* __restrict__ out,
                                             unsigned long long obase, uint64_t pol_out, ShardArgs sa = ShardArgs{N, 0u}) {
-  using GE = Geo<N>;
+  constexpr int SE = kScratchEntry<AR>;
+  using GE = Geo<N, SE>;
   constexpr int RLB = GE::RLB, LTPW = GE::LTPW;
   constexpr uint32_t TPW = GE::TPW;
   constexpr uint32_t GM = 8u / TPW - 1u;  // tile bits that select the bank group
@@ -550,11 +571,19 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
   const uint32_t o = jj / GE::NCH, whi = jj % GE::NCH;
   const uint32_t w = (whi << LTPW) | wlo;
   const uint32_t x = ((MODE == kShard) ? sa.xhi : 0u) | (k << kCB) | (o << 3) | c8;
+  auto xaddr = [&](uint32_t e) {  // exchange entry e < 512
+    if constexpr (SE == 16) return region + e * 16u;
+    else return ((e & 256u) ? twin : region) + (e & 255u) * 16u;
+  };
   typename AR::Elem v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const uint32_t R = ((uint32_t)j << RLB) | rl;
-    v[j] = AR::unpack(lds128(region + (R * TPW + tt) * 16u));
+    if constexpr (SE == 16) {
+      v[j] = AR::unpack(lds128(region + (R * TPW + tt) * 16u));
+    } else {
+      v[j] = AR::unpack_rounded(lds64(region + (R * TPW + tt) * 8u));
+    }
   }
   typename AR::Conv cv;
   if constexpr (kRegrid<AR>) {
@@ -578,11 +607,12 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
     cv = AR::make_conv(N, 0u, -N);
   }
   wht_regs<AR, 4, 16>(v);  // the four tile bits above RLB
+  if constexpr (SE == 8) __syncwarp();  // every lane's 8-byte reads are done before the region is reused
   // in-place exchange, entry (R, tt) at R' TPW + tt with R' = R_hi . (R_lo ^ (R_hi & GM))
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const uint32_t Rs = ((uint32_t)j << RLB) | (rl ^ ((uint32_t)j & GM));
-    sts128(region + (Rs * TPW + tt) * 16u, AR::pack(v[j]));
+    sts128(xaddr(Rs * TPW + tt), AR::pack(v[j]));
   }
   __syncwarp();
   const uint32_t hh = rl;  // the same lane bits now hold the low tile bits above RLB
@@ -591,7 +621,7 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
     const uint32_t Rl = (uint32_t)j & ((1u << RLB) - 1u);
     const uint32_t Rh = hh | (((uint32_t)j >> RLB) << (5 - LTPW));
     const uint32_t Rs = (Rh << RLB) | (Rl ^ (Rh & GM));
-    v[j] = AR::unpack(lds128(region + (Rs * TPW + tt) * 16u));
+    v[j] = AR::unpack(lds128(xaddr(Rs * TPW + tt)));
   }
   wht_regs<AR, RLB, 16>(v);
   // c(x, z), z = (h << 6) | w with h = (hh << RLB) | (register part)
@@ -623,7 +653,7 @@ __device__ __forceinline__ void stage2_warp(uint32_t region, uint32_t Es, uint32
 template <int N, class AR, int MODE>
 __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Shared& sh, uint32_t buf0,
                          uint32_t warp, uint32_t lane, ShardArgs sa) {
-  using GE = Geo<N>;
+  using GE = Geo<N, kScratchEntry<AR>>;
   constexpr uint32_t D = 1u << N;
   const int nbl = (MODE == kShard) ? sa.m - kCB : N - kCB, nb = 1 << nbl;  // mask blocks per matrix (or shard)
   const uint32_t team = warp / kTeamWarps, p = warp % kTeamWarps;
@@ -656,8 +686,9 @@ __device__ void consumer(void* __restrict__ out, int count, TiledCtrl* ws, Share
     } else {
       // the slot's data of this item is in shared memory: a relaxed count suffices
       if (p == 0 && lane == 0) red_relaxed_add(&ws->s2_done[s], 1);
-      stage2_warp<N, AR, MODE>(addr + p * kWarpBytes, addr + (uint32_t)GE::kChunk,
-                                addr + (uint32_t)(GE::kChunk + GE::kEOct), lane, p, (uint32_t)(it.b & (nb - 1)),
+      stage2_warp<N, AR, MODE>(addr + p * GE::kSlice, addr + (uint32_t)(GE::kChunkArea / 2) + p * GE::kSlice,
+                                addr + (uint32_t)GE::kChunkArea, addr + (uint32_t)(GE::kChunkArea + GE::kEOct), lane, p,
+                                (uint32_t)(it.b & (nb - 1)),
                                 (uint32_t)it.j, out, (unsigned long long)(it.b >> nbl) * D * ((MODE == kShard) ? 1ull << sa.m : D),
                                 pol_first, sa);
     }
@@ -717,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // MODE kUpper: G is Hermitian and read from its upper triangle.
 template <int N, class AR, int MODE = 0>
 cudaError_t launch_t(const void* G, int count, void* out, cudaStream_t st, ShardArgs sa = ShardArgs{N, 0u}) {
-  using GE = Geo<N>;
+  using GE = Geo<N, kScratchEntry<AR>>;
   void* ws = nullptr;
   cudaError_t e = tiled_workspace(st, GE::kWorkspace, &ws);
   if (e != cudaSuccess) return e;
@@ -725,7 +756,9 @@ cudaError_t launch_t(const void* G, int count, void* out, cudaStream_t st, Shard
   e = (MODE == kShard) ? tiled_tensor_map_rows(&gmap, G, sa.m, (1ll << N) * count, (int)sizeof(typename AR::Raw))
             : tiled_tensor_map(&gmap, G, N, count, (int)sizeof(typename AR::Raw));
   if (e != cudaSuccess) return e;
-  e = scratch_tensor_map4(&smap, reinterpret_cast<char*>(ws) + GE::kPBase, GE::NS * GE::NR, GE::NR, GE::TPW * 2);
+  // a warp's slice of one tile row: TPW entries in 8-byte words
+  e = scratch_tensor_map4(&smap, reinterpret_cast<char*>(ws) + GE::kPBase, GE::NS * GE::NR, GE::NR,
+                          GE::TPW * kScratchEntry<AR> / 8);
   if (e != cudaSuccess) return e;
   auto kern = twostage_kernel<N, AR, MODE>;
   constexpr size_t smem = kBufs * GE::kBuf;
