@@ -362,8 +362,10 @@ void pauli_plan_destroy(pauli_plan* plan);
  *                           and no barrier between the warps of an item. complex64 runs compensated
  *                           FP32: each value split into a high part on a per-mask power-of-two
  *                           grid, whose sums are exact, and a low part that carries the rounding
- *                           errors (error-free Fast2Sum against the grid's anchor), re-split on
- *                           the whole mask's grid between the stages. Scratch as for the tiled variants;
+ *                           errors (error-free Fast2Sum against the grid's anchor); between the
+ *                           stages each value is kept as one float per part (8 bytes: the pair
+ *                           rounded once) and split again on the whole mask's grid. Scratch as
+ *                           for the tiled variants (complex64 uses half of it);
  *                           pauli_decompose_workspace_size reports it.
  * All variants compute bit-identical complex128 results, except that the two-stage ones re-scale
  * partial sums between the stages (an extra truncation below the class quantum, well inside
